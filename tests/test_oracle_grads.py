@@ -1,0 +1,96 @@
+"""Pins of the oracle's analytic gradients against central finite differences in FP64."""
+import numpy as np
+import pytest
+
+from oracle import apmgsrn as ap
+from paper_2308_02494_gb300 import synth
+
+
+def _model(seed, M=4, R=5, C=2, H=8):
+    shape = synth.ModelShape(n_grids=M, res=R, channels=C, hidden=H)
+    p = synth.parity_model(shape, seed, shrink=0.4)
+    return p
+
+
+def _points_off_faces(p, n, seed, margin=1e-3):
+    r = np.random.default_rng(seed)
+    x = r.uniform(-1, 1, size=(4 * n, 3))
+    u = ap.local_coords(p["G"], x)
+    R = p["F"].shape[1]
+    s = (np.clip(u, -1, 1) + 1) / 2 * (R - 1)
+    frac = s - np.round(s)
+    ok = np.all(np.abs(np.abs(u) - 1.0) > margin, axis=(1, 2)) & np.all(np.abs(frac) > margin, axis=(1, 2))
+    return x[ok][:n]
+
+
+def _fd(fun, arr, idx, h):
+    a = arr.copy()
+    a[idx] += h
+    fp = fun(a)
+    a[idx] -= 2 * h
+    fm = fun(a)
+    return (fp - fm) / (2 * h)
+
+
+def test_grad_rec_matches_finite_differences():
+    p = _model(0)
+    x = _points_off_faces(p, 40, 1)
+    v = np.random.default_rng(2).uniform(0, 1, size=x.shape[0])
+    g = ap.grad_rec(p, x, v)
+
+    def L_of(name):
+        def f(a):
+            q = dict(p)
+            q[name] = a
+            return ap.loss_rec(ap.query(q, x), v)
+        return f
+
+    r = np.random.default_rng(3)
+    for name, grad in (("F", g["dF"]), ("W1", g["dW1"]), ("W2", g["dW2"]), ("w3", g["dw3"])):
+        arr = np.asarray(p[name], dtype=np.float64)
+        flat_nz = np.flatnonzero(np.abs(grad) > 1e-9 * np.abs(grad).max())
+        picks = r.choice(flat_nz, size=min(12, flat_nz.size), replace=False)
+        for fi in picks:
+            idx = np.unravel_index(fi, arr.shape)
+            h = 1e-6 * max(1.0, abs(arr[idx]))
+            fd = _fd(L_of(name), arr, idx, h)
+            assert abs(fd - grad[idx]) <= 1e-6 * np.abs(grad).max() + 1e-7 * abs(grad[idx]), (name, idx)
+    # entries untouched by every point have exactly zero gradient
+    assert np.any(g["dF"] == 0.0)
+
+
+def test_grad_density_matches_finite_differences_with_detached_target():
+    r = np.random.default_rng(4)
+    M = 3
+    G = np.zeros((M, 3, 4))
+    for d in range(3):
+        G[:, d, d] = 1.0
+    G += r.normal(0, 0.1, size=G.shape)
+    x = r.uniform(-1.1, 1.1, size=(60, 3))
+    h = r.uniform(0.0, 0.5, size=60)
+    out = ap.grad_density(G, x, h)
+    star = out["terms"]["rho_star"]
+    L0 = ap.loss_density_fixed_target(G, x, star)
+    assert abs(L0 - out["L_den"]) < 1e-12 * max(1, abs(L0))
+    f = lambda a: ap.loss_density_fixed_target(a, x, star)
+    scale = np.abs(out["dG"]).max()
+    for idx in np.ndindex(G.shape):
+        fd = _fd(f, G, idx, 1e-6)
+        assert abs(fd - out["dG"][idx]) <= 1e-6 * scale, idx
+
+
+@pytest.mark.parametrize("p", [1, 3, 10])
+def test_grad_density_other_flat_top_strengths(p):
+    r = np.random.default_rng(5 + p)
+    G = np.zeros((2, 3, 4))
+    for d in range(3):
+        G[:, d, d] = 1.0
+    G += r.normal(0, 0.1, size=G.shape)
+    x = r.uniform(-1, 1, size=(30, 3))
+    h = r.uniform(0.01, 0.5, size=30)
+    out = ap.grad_density(G, x, h, p=p)
+    star = out["terms"]["rho_star"]
+    f = lambda a: ap.loss_density_fixed_target(a, x, star, p=p)
+    scale = np.abs(out["dG"]).max()
+    for idx in np.ndindex(G.shape):
+        assert abs(_fd(f, G, idx, 1e-6) - out["dG"][idx]) <= 1e-6 * scale, idx
