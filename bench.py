@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Training-step throughput of the batched APMGSRN hot path on one GB300.
+
+Workload (default "dd8"): a synthetic 1024^3 float32 turbulence volume split into
+2x2x2 bricks of 512^3 (+2 ghost voxels), one APMGSRN per brick (M=64 grids of
+32^3 x 2 channels, MLP 128->64->64->1, BF16 grids/decoder with FP32 masters),
+uneven per-brick batches drawn from U[2^16, 2^19].  One step = sample the batch
+(Philox + Morton counting sort) -> ground truth lookup -> fused forward/backward
+of L_rec -> feature-density loss and its transform gradient -> Adam on every
+parameter, replayed from a CUDA graph.  Throughput = points of all bricks per
+second.  See the design doc for the roofline accounting.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "train fwd+bwd points/s (BF16 batched vs FP32 plain) at stated err; % roofline"
+UNIT = "points/s"
+# fused kernel: MACs per point of the 128->64->64->1 decoder, forward + backward
+MLP_MACS_FWD = 128 * 64 + 64 * 64 + 64
+MLP_MACS_BWD = 64 * 64 + 64 * 64 + 64 * 128 + 64 * 128 + 64
+FLOP_PER_POINT = 2 * (MLP_MACS_FWD + MLP_MACS_BWD)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--workload", choices=["dd8", "single-bf16", "single-fp32"], default="dd8")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP32-plain and e2e legs")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- oracle leg
+ORACLE_SNIPPET = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, %(root)r)
+from oracle import apmgsrn as ap
+from paper_2308_02494_gb300 import synth
+shape = synth.ModelShape(64, 32, 2, 64)
+p = synth.init_model(shape, 0)
+n = %(n)d
+x = synth.uniform_points(n, 1).astype(np.float64)
+vol, _ = synth.gaussian_volume(64, 16, seed=0)
+keys = ("F", "W1", "W2", "w3", "G")
+mom = {k: (np.zeros_like(p[k]), np.zeros_like(p[k])) for k in keys}
+t0 = time.perf_counter(); done = 0; reps = 0
+while True:
+    v = ap.volume_sample(vol, x)
+    g = ap.grad_rec(p, x, v)
+    d = ap.grad_density(p["G"], x, g["h"])
+    grads = {"F": g["dF"], "W1": g["dW1"], "W2": g["dW2"], "w3": g["dw3"], "G": d["dG"]}
+    for k in keys:
+        lr = 1e-3 if k == "G" else 1e-2
+        p[k], m1, m2 = ap.adam_update(p[k], grads[k], mom[k][0], mom[k][1], reps + 1, lr)
+        mom[k] = (m1, m2)
+    done += n; reps += 1
+    if time.perf_counter() - t0 >= %(budget)f:
+        break
+print(json.dumps({"points": done, "seconds": time.perf_counter() - t0, "reps": reps}))
+"""
+
+
+def oracle_rate(budget_s: float, n: int = 2048):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET % {"root": ROOT, "n": n, "budget": budget_s}
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    sample = (f"FP64 oracle, 1 thread: one brick's model (M=64, R=32, C=2, 128->64->64->1), "
+              f"{n}-point batches x {r['reps']} reps: target lookup + fwd + L_rec bwd + density bwd + "
+              f"Adam over all 4.2M parameters, {r['seconds']:.1f} s")
+    return r["points"] / r["seconds"], sample
+
+
+def run_reference(args, workload):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rates = []
+    budget = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(max(1, args.steps)):
+        rate, sample = oracle_rate(budget)
+        rates.append(rate)
+    value = sum(rates) / len(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 8:
+                continue
+            for nm, val in zip(names, r[4:8]):
+                if val.strip().lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- own leg
+def workload_of(name):
+    if name == "dd8":
+        return {"workload": "dd8: 8 bricks (2x2x2 of a 1024^3 Fourier volume, ghost 2), per-brick "
+                            "batches U[2^16,2^19], M=64 R=32 C=2, MLP 128-64-64-1, BF16, density phase",
+                "bricks": 8, "volume": 1024, "grids": 64, "res": 32, "channels": 2, "precision": "bf16",
+                "l2": "inputs larger than L2 (4 GiB volume; 1.1 GB of parameters and Adam state streamed per step)"}
+    if name == "single-bf16":
+        return {"workload": "single model, 512^3 Fourier volume, N=2^18, M=64 R=32 C=2, BF16, density phase",
+                "bricks": 1, "volume": 512, "grids": 64, "res": 32, "channels": 2, "precision": "bf16",
+                "l2": "inputs larger than L2 (512 MiB volume)"}
+    return {"workload": "single model, 512^3 Fourier volume, N=2^18, M=64 R=32 C=2, FP32, density phase",
+            "bricks": 1, "volume": 512, "grids": 64, "res": 32, "channels": 2, "precision": "fp32",
+            "l2": "inputs larger than L2 (512 MiB volume)"}
+
+
+def setup(wl, seed_offset=0):
+    import numpy as np
+    import torch
+    from paper_2308_02494_gb300 import synth
+    from paper_2308_02494_gb300.model import SRN
+
+    shape = synth.ModelShape(wl["grids"], wl["res"], wl["channels"], 64)
+    vox = wl["volume"]
+    modes = synth.fourier_modes(256, 1, 64, seed=0)
+    vol, _, _ = synth.fourier_volume(vox, modes, device="cuda")
+    if wl["bricks"] == 8:
+        boxes = synth.brick_boxes(vox, (2, 2, 2), ghost=2)
+        counts = synth.uneven_counts(8, 1 << 16, 1 << 19, seed=1 + seed_offset)
+    else:
+        boxes = np.array([[0, 0, 0, vox - 1, vox - 1, vox - 1]], dtype=np.int64)
+        counts = np.array([1 << 18], dtype=np.int64)
+    n_total = int(counts.sum())
+    m = SRN(shape, n_bricks=wl["bricks"], precision=wl["precision"], max_points=n_total)
+    m.set_params([synth.init_model(shape, 100 + b + seed_offset) for b in range(wl["bricks"])])
+    off = SRN.offsets_of(counts)
+    xyz = torch.empty((n_total, 3), dtype=torch.float32, device="cuda")
+    tgt = torch.empty(n_total, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    return m, vol, boxes, off, xyz, tgt, n_total
+
+
+def time_steps(m, vol, boxes, off, xyz, tgt, steps, warmup, stream, sync_all):
+    import torch
+    with torch.cuda.stream(stream):
+        for i in range(warmup):
+            m.train_step(7, vol, boxes, off, True, xyz, tgt, stream=stream)
+        stream.synchronize()
+        sync_all()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for i in range(steps):
+            m.train_step(7, vol, boxes, off, True, xyz, tgt, stream=stream)
+        ev1.record(stream)
+        stream.synchronize()
+    sync_all()
+    return ev0.elapsed_time(ev1)
+
+
+def run_own(args, workload):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2308_02494_gb300 import srn as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    wl = workload
+    m, vol, boxes, off, xyz, tgt, n_total = setup(wl, seed_offset=0)
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    # warm up (first call eager, second captures the CUDA graph, the rest replay it)
+    time_steps(m, vol, boxes, off, xyz, tgt, 0, max(3, args.warmup), stream, sync_all)
+    clocks.start()
+    ms = time_steps(m, vol, boxes, off, xyz, tgt, args.steps, 0, stream, sync_all)
+    clk = clocks.stop()
+    m.status(stream)
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = n_total * world * args.steps / (ms / 1e3)
+    losses = m.losses.cpu().numpy()
+
+    # dominant kernel: CUDA events around every fused-kernel launch of eager steps
+    k_steps = min(args.steps, 50)
+    S.srn_set_timing(m.handle, True)
+    dflt = torch.cuda.default_stream()
+    for _ in range(k_steps):
+        m.train_step(7, vol, boxes, off, True, xyz, tgt, stream=dflt)
+    torch.cuda.synchronize()
+    k_ms, k_n = S.srn_read_timing(m.handle)
+    S.srn_set_timing(m.handle, False)
+    k_avg = k_ms / max(1, k_n)
+    hbm, tf_burst, tf_sus, src = peaks()
+    achieved_tf = FLOP_PER_POINT * n_total / (k_avg / 1e3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved_tf, "peak": tf_sus, "unit": "TFLOP/s",
+            "frac": achieved_tf / tf_sus, "traffic": None, "kernel": "k_query_bf16<128, train+density>",
+            "kernel_ms": k_avg, "peak_source": f"{src} bf16 sustained",
+            "per_point": f"{FLOP_PER_POINT} flop (decoder fwd+bwd MACs x2)"}
+
+    # end to end through the C ABI: pinned host points/targets -> device, backward+step, losses -> host
+    e2e = None
+    fp32_plain = None
+    if not args.no_extras:
+        m.sample_points(11, 0, off, xyz)
+        m.sample_target(vol, boxes, xyz, off, tgt)
+        torch.cuda.synchronize()
+        hx = xyz.cpu().pin_memory()
+        ht = tgt.cpu().pin_memory()
+        hl = torch.empty_like(m.losses, device="cpu").pin_memory()
+        e_steps = min(args.steps, 50)
+        with torch.cuda.stream(stream):
+            for it in range(3 + e_steps):
+                if it == 3:
+                    stream.synchronize()
+                    t0 = time.perf_counter()
+                xyz.copy_(hx, non_blocking=True)
+                tgt.copy_(ht, non_blocking=True)
+                m.backward(xyz, tgt, off, density=True, stream=stream)
+                m.step(density=True, stream=stream)
+                hl.copy_(m.losses, non_blocking=True)
+            stream.synchronize()
+            el = time.perf_counter() - t0
+        e2e = {"value": n_total * world * e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(hx.numel() * 4 + ht.numel() * 4),
+               "d2h_bytes_per_step": int(hl.numel() * 8),
+               "path": "srn_backward(SRN_DENSITY) + srn_step with host-pinned points/targets, losses read back"}
+        # the plain FP32 single-model path (the speedup denominator)
+        del m, vol
+        torch.cuda.empty_cache()
+        wl32 = workload_of("single-fp32")
+        m2, vol2, boxes2, off2, xyz2, tgt2, n2 = setup(wl32)
+        s2 = torch.cuda.Stream()
+        time_steps(m2, vol2, boxes2, off2, xyz2, tgt2, 0, 3, s2, sync_all)
+        ms2 = time_steps(m2, vol2, boxes2, off2, xyz2, tgt2, min(args.steps, 40), 0, s2, sync_all)
+        fp32_plain = {"value": n2 * min(args.steps, 40) / (ms2 / 1e3), "unit": UNIT,
+                      "workload": wl32["workload"]}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1:
+        rate, sample = oracle_rate(args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    cfg = dict(wl)
+    cfg["points_per_step"] = n_total
+    cfg["parallelism"] = f"bricks replicated per GPU x{world}" if world > 1 else "1 GPU"
+    if fp32_plain:
+        cfg["fp32_plain"] = fp32_plain
+        cfg["speedup_vs_fp32_plain"] = value / world / fp32_plain["value"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": wl["precision"], "data": "synthetic",
+            "config": cfg, "clocks": clk, "e2e": e2e, "gpu_launches": 10 * args.steps,
+            "roofline": roof, "cpu_baseline": cpu,
+            "last_losses": {"L_rec_mean": float(np.mean(losses[:, 0])), "L_den_mean": float(np.mean(losses[:, 1]))}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    wl = workload_of(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+    run_own(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * srn.h -- C ABI of libsrn, the GB300 (sm_103a) implementation of the APMGSRN
+ * point query (Wurster et al., "Adaptively Placed Multi-Grid Scene Representation
+ * Networks for Large-Scale Data Visualization"), its training step and its renderer.
+ *
+ * Conventions shared by every entry point
+ *   - All pointers named *_dev point to device memory; all others to host memory.
+ *   - The caller owns every buffer (parameters, gradients, Adam moments, BF16
+ *     shadow, workspace, inputs, outputs).  The handle keeps non-owning pointers.
+ *   - Calls taking a `stream` (a cudaStream_t passed as void*) are asynchronous on
+ *     that stream; NULL means the legacy default stream.  They return SRN_OK once
+ *     the work is enqueued.  Arguments are validated before anything is launched;
+ *     a bad argument returns SRN_ERR_INVALID_ARG (or SRN_ERR_UNSUPPORTED for a
+ *     legal but unimplemented shape) with nothing enqueued.  A launch failure
+ *     returns SRN_ERR_CUDA.  srn_last_error() gives a message for the calling thread.
+ *   - Nothing throws across the ABI.  No entry point allocates device memory.
+ *   - Layouts (all row-major, C order):
+ *       points   xyz[N][3] float32, points of brick b contiguous in
+ *                [offsets[b], offsets[b+1]); coordinates in the brick's local
+ *                domain [-1, 1]^3 (Sec. 4.1: a model maps [-1,1]^3 to a scalar).
+ *       features F[B][M][R][R][R][C]: grid i, node (z, y, x), channel c; the
+ *                local coordinate u_x runs along the fastest node axis.
+ *       transforms G[B][M][3][4]: first three rows of the 4x4 matrix of Eq. 1.
+ *       decoder  W1[B][H][K], W2[B][H][H], w3[B][H] (K = M*C, H = 64), no biases.
+ */
+#ifndef SRN_H
+#define SRN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SRN_MAX_BRICKS 64
+
+typedef struct srn_handle srn_handle;
+
+typedef enum {
+  SRN_OK = 0,
+  SRN_ERR_INVALID_ARG = 1,     /* null pointer, bad size, inconsistent offsets */
+  SRN_ERR_UNSUPPORTED = 2,     /* legal shape this build does not implement */
+  SRN_ERR_CUDA = 3,            /* a CUDA call or launch failed */
+  SRN_ERR_DEVICE_TIMEOUT = 4,  /* reserved: no kernel of this build waits on another */
+  SRN_ERR_NONFINITE = 5,       /* a loss came out NaN/Inf (reported by srn_get_status) */
+  SRN_ERR_STATE = 6            /* call out of order (e.g. step before any backward) */
+} srn_status;
+
+typedef enum { SRN_FP32 = 0, SRN_BF16 = 1 } srn_precision;
+
+/* Flags of srn_backward / srn_step / srn_train_step. */
+#define SRN_DENSITY 1u   /* step (2) of Sec. 4.3.2: L_den (Eq. 9) and its gradient into G */
+#define SRN_UPSTREAM 2u  /* srn_backward only: target_dev holds dL/df per point (any upstream
+                            loss) instead of v(x); no L_rec is formed; excludes SRN_DENSITY */
+
+/* Model and optimiser configuration (Sec. 4.1, 4.2, 6).  Supported in this build:
+ * hidden = 64; channels in {1, 2}; K = n_grids*channels in {16, 32, 64, 128};
+ * 2 <= res <= 64; 1 <= flat_top_p <= 16; 1 <= n_bricks <= SRN_MAX_BRICKS. */
+typedef struct {
+  int32_t n_bricks;      /* B: independent models trained and queried together (Sec. 5) */
+  int32_t n_grids;       /* M feature grids per model (Sec. 4.1.1) */
+  int32_t channels;      /* C features per grid node */
+  int32_t res;           /* R: every grid is R x R x R nodes */
+  int32_t hidden;        /* H neurons in each of the two hidden layers (Sec. 4.1.2) */
+  int32_t precision;     /* srn_precision: FP32 everywhere, or BF16 grids/decoder */
+  int32_t flat_top_p;    /* p of Eq. 7; the exponent is 2p (the paper uses p = 10) */
+  float density_eps;     /* epsilon of Eq. 8 (also used inside Eq. 9's log) */
+  float lr_feat;         /* Adam learning rate of F and the decoder (0.01, Sec. 6) */
+  float lr_xform;        /* Adam learning rate of G (0.001, Sec. 6) */
+  float beta1, beta2;    /* Adam betas (0.9, 0.99, Sec. 6) */
+  float adam_eps;        /* Adam epsilon (not given in the paper; 1e-8 by default) */
+} srn_config;
+
+/* Element offsets into the flat float32 parameter buffer.  The gradient and the two
+ * Adam moment buffers use the same layout.  [0, n_group_a) holds every F and
+ * decoder tensor (learning rate lr_feat; the BF16 shadow mirrors this range);
+ * [n_group_a, n_params) holds every G (learning rate lr_xform).  Brick b's copy of
+ * tensor X starts at off_X + b * size_X.  Every offset is a multiple of 64. */
+typedef struct {
+  int64_t n_params, n_group_a;
+  int64_t off_F, off_W1, off_W2, off_w3, off_G;
+  int64_t size_F, size_W1, size_W2, size_w3, size_G;
+} srn_layout;
+
+/* Caller-owned device tensors (see srn_layout). */
+typedef struct {
+  float* params_dev;       /* [n_params] float32 master weights */
+  float* grads_dev;        /* [n_params] written by srn_backward */
+  float* adam_m_dev;       /* [n_params] first moments, zero-initialised by the caller */
+  float* adam_v_dev;       /* [n_params] second moments, zero-initialised by the caller */
+  uint16_t* shadow_dev;    /* [n_group_a] bfloat16 copy read by the BF16 kernels; NULL for FP32 */
+  const float* range_dev;  /* [B][2] saved (min, max) of each brick's data (Sec. 4.1.2 "Scaling") */
+} srn_tensors;
+
+/* Pinhole or orthographic camera (Sec. 6): eye position and an orthonormal basis.
+ * scale = tan(fov/2) (perspective) or half the view height (orthographic). */
+typedef struct {
+  float eye[3], forward[3], right[3], up[3];
+  float scale;
+  int32_t ortho;
+} srn_camera;
+
+/* Fill *out with the parameter layout of cfg.  Host only. */
+srn_status srn_param_layout(const srn_config* cfg, srn_layout* out);
+
+/* Bytes of device workspace srn_create needs for batches of up to max_points
+ * points (all bricks together) and renders of up to max_points samples per pass. */
+srn_status srn_workspace_size(const srn_config* cfg, int64_t max_points, size_t* bytes);
+
+/* Create a handle over caller-owned tensors and a workspace of at least
+ * srn_workspace_size(cfg, max_points) bytes (256-byte aligned).  Zeroes the device
+ * step counters in the workspace with a synchronous memset. */
+srn_status srn_create(const srn_config* cfg, const srn_tensors* tensors, void* workspace_dev,
+                      size_t workspace_bytes, int64_t max_points, srn_handle** out);
+
+/* Destroy a handle (frees its host state and cached CUDA graphs; no device buffer). */
+srn_status srn_destroy(srn_handle* h);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* srn_last_error(void);
+
+/* Re-derive the BF16 shadow of [0, n_group_a) from the float32 master (call after
+ * writing parameters by hand).  A no-op for FP32 handles. */
+srn_status srn_sync_shadow(srn_handle* h, void* stream);
+
+/* Batch sampling (Sec. 6 "Training": points uniform in [-1,1]^3 each iteration).
+ * Point n of brick b at this step comes from Philox4x32-10 with counter
+ * (n, b, step, 0) and key (seed, seed >> 32); coordinate d = 2 (r_d >> 8) 2^-24 - 1.
+ * Within each brick the points are then reordered by the Morton code of their
+ * 32^3 bin, which does not change the batch as a set.  offsets[B+1] (host):
+ * brick b gets offsets[b+1] - offsets[b] points, offsets[B] <= max_points.
+ * If step_dev is non-NULL the step is read from device memory (graph replays). */
+srn_status srn_sample_points(srn_handle* h, void* stream, uint64_t seed, uint64_t step,
+                             const uint64_t* step_dev, const int64_t* offsets, float* xyz_dev);
+
+/* Ground truth v(x) of Sec. 4.3.1: trilinear interpolation of a float32 volume
+ * [dims[2]][dims[1]][dims[0]] (x fastest).  Brick b's local [-1,1]^3 spans the
+ * inclusive voxel box boxes[b] = (lo_x, lo_y, lo_z, hi_x, hi_y, hi_z) (host
+ * [B][6]; hi > lo per axis), corner-aligned (Sec. 5.1: ghost cells included). */
+srn_status srn_sample_target(srn_handle* h, void* stream, const float* volume_dev,
+                             const int64_t dims[3], const int64_t* boxes,
+                             const float* xyz_dev, const int64_t* offsets, float* target_dev);
+
+/* Forward query f(x) = d(e(x)) (Eq. 1-3 and Sec. 4.1.2) of every brick's points:
+ * out_dev[n] for xyz_dev[n].  offsets as in srn_sample_points. */
+srn_status srn_forward(srn_handle* h, void* stream, const float* xyz_dev,
+                       const int64_t* offsets, float* out_dev);
+
+/* Forward, L_rec (Sec. 4.3.1) and its gradient into F and the decoder (step (1) of
+ * Sec. 4.3.2), written (not accumulated) into the gradient buffer.  With
+ * SRN_UPSTREAM the gradient is instead that of any loss whose dL/df is given.  With
+ * SRN_DENSITY it also evaluates L_den (Eq. 7-9, with h(x) = (f(x) - v(x))^2 and the
+ * target rho* held constant) and writes its gradient into G (step (2)); without it
+ * G's gradient is zero.  losses_dev (device [B][4] float64, may be NULL) receives
+ * per brick (L_rec, L_den, sum of rho over the batch, point count). */
+srn_status srn_backward(srn_handle* h, void* stream, const float* xyz_dev,
+                        const float* target_dev, const int64_t* offsets, uint32_t flags,
+                        double* losses_dev);
+
+/* One Adam step (Sec. 6: beta = (0.9, 0.99), lr 0.01 for F and the decoder) on
+ * [0, n_group_a); with SRN_DENSITY also on G (lr 0.001), whose bias correction
+ * counts only the steps that updated it.  Refreshes the BF16 shadow. */
+srn_status srn_step(srn_handle* h, void* stream, uint32_t flags);
+
+/* One whole training iteration: sample -> target -> backward -> Adam, with the
+ * sampler step read from the device counter that srn_step advances.  On a
+ * non-default stream the sequence is captured once per (flags, offsets, volume)
+ * into a CUDA graph and replayed.  losses_dev as in srn_backward. */
+srn_status srn_train_step(srn_handle* h, void* stream, uint64_t seed, const float* volume_dev,
+                          const int64_t dims[3], const int64_t* boxes, const int64_t* offsets,
+                          uint32_t flags, float* xyz_dev, float* target_dev, double* losses_dev);
+
+/* Headless volume render (Sec. 6) of the domain decomposition (Sec. 5.3) into
+ * rgba_dev [height][width][4].  Each ray is clipped to [-1,1]^3 and sampled at
+ * `samples` midpoints; every sample is hashed to its brick (grid[3] = I, J, K,
+ * B = I J K) and mapped into that brick's local domain using boxes[B][6] inside a
+ * volume of `vox` voxels per axis; the value is mapped through the 256 x RGBA
+ * lut_dev between vmin and vmax and composited front to back with
+ * alpha = 1 - exp(-a dt / (2/512)).  Batches of at most max_points samples. */
+srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const float* lut_dev,
+                      float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
+                      const int32_t grid[3], const int64_t* boxes, int64_t vox, float* rgba_dev);
+
+/* Measurement hook (no counterpart in the paper).  While enabled, every launch of
+ * the fused query kernel (srn_forward / srn_backward, also inside srn_train_step
+ * when it runs eagerly) outside stream capture is bracketed by CUDA events on its
+ * stream.  srn_read_timing synchronises on the recorded events and returns the
+ * summed kernel time in milliseconds and the number of launches since the last
+ * read (then resets both).  Enabling or disabling clears the counters. */
+srn_status srn_set_timing(srn_handle* h, int32_t enable);
+srn_status srn_read_timing(srn_handle* h, double* total_ms, int64_t* launches);
+
+/* Synchronise `stream` and report device-side status: SRN_ERR_NONFINITE if a loss
+ * computed since the last call was NaN/Inf (the flag is then cleared), else SRN_OK. */
+srn_status srn_get_status(srn_handle* h, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SRN_H */

@@ -1,0 +1,422 @@
+// libsrn kernels around the fused query:
+//   * density loss passes 2 and 3 (Eq. 8, Eq. 9 and dL_den/dG) and the per-brick
+//     finalisation (losses, dG from the float64 sums);
+//   * Adam (Sec. 6) over the flat parameter buffer, plus the BF16 shadow refresh;
+//   * the batch sampler (Philox4x32-10, then a counting sort by 32^3 Morton bin);
+//   * the ground-truth lookup v(x) of Sec. 4.3.1 (trilinear in a float32 volume).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace srn {
+namespace {
+
+__device__ __forceinline__ int brick_of_point(const Bricks& br, int64_t g) {
+  int lo = 0, hi = br.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (br.off[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename Tv>
+__device__ __forceinline__ Tv warp_sum(Tv v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------ density pass 2
+// Per point: rho_s = rho/S, k = hbar/(h+eps), rho* = exp(k log(rho_s+eps)) (held
+// constant), g = dL/drho_s = -rho*/(N (rho_s+eps)).  Sums per brick:
+// c = sum g rho_s (needed by dL/drho = (g - c)/S) and L_den = mean rho* (k-1) log(rho_s+eps).
+__global__ void k_density_scalar(Bricks br, TrainWs ws, float eps) {
+  const int64_t total = br.off[br.n];
+  double c_acc = 0.0, l_acc = 0.0;
+  int cur = -1;
+  for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ; gi += (int64_t)gridDim.x * blockDim.x) {
+    const bool live = gi < total;
+    const int b = live ? brick_of_point(br, gi) : -1;
+    // flush when the brick changes (warp-uniform flushes are not guaranteed, so
+    // each thread flushes its own partial with a float64 atomic)
+    if (b != cur) {
+      if (cur >= 0) {
+        atomicAdd(ws.acc + cur * kAccPerBrick + ACC_C, c_acc);
+        atomicAdd(ws.acc + cur * kAccPerBrick + ACC_LDEN, l_acc);
+      }
+      c_acc = 0.0; l_acc = 0.0; cur = b;
+    }
+    if (!live) break;
+    const double n = (double)(br.off[b + 1] - br.off[b]);
+    const double S = ws.acc[b * kAccPerBrick + ACC_SUM_RHO];
+    const double hbar = ws.acc[b * kAccPerBrick + ACC_SUM_R2] / n;
+    const double rs = (double)ws.rho[gi] / S;
+    const double k = hbar / ((double)ws.herr[gi] + (double)eps);
+    const double lr = log(rs + (double)eps);
+    const double star = exp(k * lr);
+    const double g = -star / (n * (rs + (double)eps));
+    c_acc += g * rs;
+    l_acc += star * (k - 1.0) * lr / n;
+  }
+}
+
+// ------------------------------------------------------------ density pass 3
+// dL/drho_n = q_n = (g_n - c)/S.  For grid i, with E = exp(-sum_d u_d^2p) and
+// e_d = 2p u_d^(2p-1): dL/dA_i = det_i (A_i^{-T} sum q E - sum q E e x^T),
+// dL/dt_i = -det_i sum q E e.  This pass accumulates, per brick and grid, the 13
+// sums  sum qE,  sum qE e_d,  sum qE e_d x_e  (float32 per thread, float64 across).
+constexpr int DT = 128;   // points per tile
+constexpr int DNT = 256;  // threads
+
+__global__ void __launch_bounds__(DNT)
+k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, float eps) {
+  __shared__ TileMap tm;
+  __shared__ float4 sx[DT];
+  __shared__ float sq[DT];
+  __shared__ float sg[kMaxGrids * 12];
+  __shared__ double red[DNT];
+  const int tid = threadIdx.x, M = md.M;
+  const int npg = DNT / M;             // point groups (M divides 256)
+  const int gi = tid % M, pg = tid / M;
+  if (tid == 0) build_tile_map(br, DT, tm);
+  __syncthreads();
+  const int total = tm.first[br.n];
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int tb = blockIdx.x * per, te = min(total, tb + per);
+  float acc[13];
+#pragma unroll
+  for (int j = 0; j < 13; ++j) acc[j] = 0.f;
+
+  auto flush = [&](int b) {
+    for (int j = 0; j < 13; ++j) {
+      red[tid] = (double)acc[j];
+      acc[j] = 0.f;
+      __syncthreads();
+      if (pg == 0) {
+        double s = 0.0;
+        for (int q = 0; q < npg; ++q) s += red[q * M + gi];
+        atomicAdd(ws.gsum + ((int64_t)b * M + gi) * 13 + j, s);
+      }
+      __syncthreads();
+    }
+  };
+
+  int cur = -1;
+  double S = 1.0, hbar = 0.0, c = 0.0, n = 1.0;
+  for (int tile = tb; tile < te; ++tile) {
+    const int b = brick_of_tile(tm, br.n, tile, cur);
+    if (b != cur) {
+      if (cur >= 0) flush(cur);
+      cur = b;
+      for (int k = tid; k < M * 12; k += DNT) sg[k] = md.G[(int64_t)b * md.sG + k];
+      n = (double)(br.off[b + 1] - br.off[b]);
+      S = ws.acc[b * kAccPerBrick + ACC_SUM_RHO];
+      hbar = ws.acc[b * kAccPerBrick + ACC_SUM_R2] / n;
+      c = ws.acc[b * kAccPerBrick + ACC_C];
+      __syncthreads();
+    }
+    const int64_t p0 = br.off[b] + (int64_t)(tile - tm.first[b]) * DT;
+    const int np = (int)min((int64_t)DT, br.off[b + 1] - p0);
+    if (tid < DT) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      float q = 0.f;
+      if (tid < np) {
+        const int64_t gp = p0 + tid;
+        v = make_float4(xyz[3 * gp], xyz[3 * gp + 1], xyz[3 * gp + 2], 0.f);
+        const double rs = (double)ws.rho[gp] / S;
+        const double k = hbar / ((double)ws.herr[gp] + (double)eps);
+        const double star = exp(k * log(rs + (double)eps));
+        const double g = -star / (n * (rs + (double)eps));
+        q = (float)((g - c) / S);
+      }
+      sx[tid] = v;
+      sq[tid] = q;
+    }
+    __syncthreads();
+    const float* gg = sg + 12 * gi;
+    for (int p = pg; p < np; p += npg) {
+      const float4 x = sx[p];
+      float ux, uy, uz, ex, ey, ez;
+      affine(gg, x.x, x.y, x.z, ux, uy, uz);
+      const float E = flat_top(ux, uy, uz, md.p, &ex, &ey, &ez);
+      const float w = sq[p] * E;
+      if (w == 0.f) continue;
+      const float wx = w * ex, wy = w * ey, wz = w * ez;
+      acc[0] += w;
+      acc[1] += wx; acc[2] += wy; acc[3] += wz;
+      acc[4] = fmaf(wx, x.x, acc[4]); acc[5] = fmaf(wx, x.y, acc[5]); acc[6] = fmaf(wx, x.z, acc[6]);
+      acc[7] = fmaf(wy, x.x, acc[7]); acc[8] = fmaf(wy, x.y, acc[8]); acc[9] = fmaf(wy, x.z, acc[9]);
+      acc[10] = fmaf(wz, x.x, acc[10]); acc[11] = fmaf(wz, x.y, acc[11]); acc[12] = fmaf(wz, x.z, acc[12]);
+    }
+    __syncthreads();
+  }
+  if (cur >= 0) flush(cur);
+}
+
+// ------------------------------------------------------------ finalisation
+// One block per brick: losses and (with the density step) dG from the sums.
+__global__ void k_finalize(Bricks br, Model md, TrainWs ws, int density, float* dG, int64_t sdG,
+                           double* losses) {
+  const int b = blockIdx.x, i = threadIdx.x;
+  const double n = (double)(br.off[b + 1] - br.off[b]);
+  const double* acc = ws.acc + b * kAccPerBrick;
+  if (density && i < md.M) {
+    const float* g = md.G + (int64_t)b * md.sG + 12 * i;
+    const double a00 = g[0], a01 = g[1], a02 = g[2], a10 = g[4], a11 = g[5], a12 = g[6];
+    const double a20 = g[8], a21 = g[9], a22 = g[10];
+    // cofactors: det * A^{-T} is the cofactor matrix
+    const double c00 = a11 * a22 - a12 * a21, c01 = a12 * a20 - a10 * a22, c02 = a10 * a21 - a11 * a20;
+    const double c10 = a02 * a21 - a01 * a22, c11 = a00 * a22 - a02 * a20, c12 = a01 * a20 - a00 * a21;
+    const double c20 = a01 * a12 - a02 * a11, c21 = a02 * a10 - a00 * a12, c22 = a00 * a11 - a01 * a10;
+    const double det = a00 * c00 + a01 * c01 + a02 * c02;
+    const double* s = ws.gsum + ((int64_t)b * md.M + i) * 13;
+    float* d = dG + (int64_t)b * sdG + 12 * i;
+    const double cof[3][3] = {{c00, c01, c02}, {c10, c11, c12}, {c20, c21, c22}};
+    for (int r = 0; r < 3; ++r) {
+      for (int e = 0; e < 3; ++e) d[4 * r + e] = (float)(cof[r][e] * s[0] - det * s[4 + 3 * r + e]);
+      d[4 * r + 3] = (float)(-det * s[1 + r]);
+    }
+  }
+  if (i == 0) {
+    const double lrec = acc[ACC_SUM_R2] / n;
+    const double lden = density ? acc[ACC_LDEN] : 0.0;
+    if (!isfinite(lrec) || !isfinite(lden)) atomicOr(ws.status, 1);
+    if (losses) {
+      losses[4 * b + 0] = lrec;
+      losses[4 * b + 1] = lden;
+      losses[4 * b + 2] = density ? acc[ACC_SUM_RHO] : 0.0;
+      losses[4 * b + 3] = n;
+    }
+  }
+}
+
+// ------------------------------------------------------------ Adam
+__global__ void k_advance(StepState* st, int do_b) {
+  st->step += 1;
+  st->t_a += 1;
+  if (do_b) st->t_b += 1;
+}
+
+__device__ __forceinline__ float adam1(float& p, float g, float& m, float& v, float lr, float b1,
+                                       float b2, float eps, float bc1, float rbc2) {
+  m = fmaf(b1, m, (1.f - b1) * g);
+  v = fmaf(b2, v, (1.f - b2) * g * g);
+  const float mh = m / bc1;
+  const float vh = v * rbc2;
+  p -= lr * mh / (sqrtf(vh) + eps);
+  return p;
+}
+
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, uint16_t* __restrict__ shadow, int64_t n_a,
+                       int64_t n_total, int do_b, float lr_a, float lr_b, float b1, float b2,
+                       float eps, const StepState* st) {
+  const int ta = st->t_a, tbc = st->t_b;
+  const float bc1a = (float)(1.0 - pow((double)b1, ta)), rbc2a = (float)(1.0 / (1.0 - pow((double)b2, ta)));
+  const float bc1b = (float)(1.0 - pow((double)b1, tbc > 0 ? tbc : 1));
+  const float rbc2b = (float)(1.0 / (1.0 - pow((double)b2, tbc > 0 ? tbc : 1)));
+  const int64_t end = do_b ? n_total : n_a;
+  const int64_t n4 = end / 4;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = 4 * q;
+    float4 P = reinterpret_cast<float4*>(p)[q];
+    const float4 Gd = reinterpret_cast<const float4*>(g)[q];
+    float4 Mm = reinterpret_cast<float4*>(m)[q];
+    float4 V = reinterpret_cast<float4*>(v)[q];
+    const bool a = i < n_a;   // n_a is a multiple of 64, so a float4 never straddles groups
+    const float lr = a ? lr_a : lr_b, bc1 = a ? bc1a : bc1b, rbc2 = a ? rbc2a : rbc2b;
+    adam1(P.x, Gd.x, Mm.x, V.x, lr, b1, b2, eps, bc1, rbc2);
+    adam1(P.y, Gd.y, Mm.y, V.y, lr, b1, b2, eps, bc1, rbc2);
+    adam1(P.z, Gd.z, Mm.z, V.z, lr, b1, b2, eps, bc1, rbc2);
+    adam1(P.w, Gd.w, Mm.w, V.w, lr, b1, b2, eps, bc1, rbc2);
+    reinterpret_cast<float4*>(p)[q] = P;
+    reinterpret_cast<float4*>(m)[q] = Mm;
+    reinterpret_cast<float4*>(v)[q] = V;
+    if (shadow && a) {
+      uint2 s;
+      s.x = pack_bf16(P.x, P.y);
+      s.y = pack_bf16(P.z, P.w);
+      reinterpret_cast<uint2*>(shadow)[q] = s;
+    }
+  }
+}
+
+__global__ void k_shadow(const float* __restrict__ p, uint16_t* __restrict__ shadow, int64_t n) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n / 4; q += (int64_t)gridDim.x * blockDim.x) {
+    const float4 P = reinterpret_cast<const float4*>(p)[q];
+    uint2 s;
+    s.x = pack_bf16(P.x, P.y);
+    s.y = pack_bf16(P.z, P.w);
+    reinterpret_cast<uint2*>(shadow)[q] = s;
+  }
+}
+
+// ------------------------------------------------------------ sampler
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 5 bits -> every third bit
+  v &= 0x1f;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__device__ __forceinline__ uint32_t morton_bin(float x, float y, float z) {
+  const float s = (float)(1 << kSortBits) * 0.5f;
+  const uint32_t ix = (uint32_t)min((int)((x + 1.f) * s), (1 << kSortBits) - 1);
+  const uint32_t iy = (uint32_t)min((int)((y + 1.f) * s), (1 << kSortBits) - 1);
+  const uint32_t iz = (uint32_t)min((int)((z + 1.f) * s), (1 << kSortBits) - 1);
+  return spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+}
+
+__global__ void k_sample_gen(Bricks br, unsigned long long seed, unsigned long long step,
+                             const unsigned long long* step_dev, float* tmp, uint32_t* rank,
+                             uint32_t* hist) {
+  const int64_t total = br.off[br.n];
+  const unsigned long long s = step_dev ? *step_dev : step;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x) {
+    const int b = brick_of_point(br, gi);
+    const uint32_t n = (uint32_t)(gi - br.off[b]);
+    const uint4 r = philox(make_uint4(n, (uint32_t)b, (uint32_t)s, 0u), key);
+    const float x = fmaf((float)(r.x >> 8), 0x1p-23f, -1.f);
+    const float y = fmaf((float)(r.y >> 8), 0x1p-23f, -1.f);
+    const float z = fmaf((float)(r.z >> 8), 0x1p-23f, -1.f);
+    tmp[3 * gi] = x; tmp[3 * gi + 1] = y; tmp[3 * gi + 2] = z;
+    rank[gi] = atomicAdd(hist + (int64_t)b * kSortBins + morton_bin(x, y, z), 1u);
+  }
+}
+
+// Exclusive scan of one brick's kSortBins counters (one block of 1024 threads per brick).
+__global__ void __launch_bounds__(1024) k_sample_scan(uint32_t* hist) {
+  __shared__ uint32_t part[1024];
+  constexpr int per = kSortBins / 1024;
+  uint32_t* h = hist + (int64_t)blockIdx.x * kSortBins + threadIdx.x * per;
+  uint32_t loc[per];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < per; ++k) { loc[k] = s; s += h[k]; }
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {   // Hillis-Steele inclusive scan
+    const uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  const uint32_t base = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+#pragma unroll
+  for (int k = 0; k < per; ++k) h[k] = base + loc[k];
+}
+
+__global__ void k_sample_scatter(Bricks br, const float* __restrict__ tmp, const uint32_t* __restrict__ rank,
+                                 const uint32_t* __restrict__ hist, float* __restrict__ xyz) {
+  const int64_t total = br.off[br.n];
+  for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x) {
+    const int b = brick_of_point(br, gi);
+    const float x = tmp[3 * gi], y = tmp[3 * gi + 1], z = tmp[3 * gi + 2];
+    const int64_t dst = br.off[b] + hist[(int64_t)b * kSortBins + morton_bin(x, y, z)] + rank[gi];
+    xyz[3 * dst] = x; xyz[3 * dst + 1] = y; xyz[3 * dst + 2] = z;
+  }
+}
+
+// ------------------------------------------------------------ ground truth v(x)
+__global__ void k_target(Bricks br, const float* __restrict__ vol, int64_t dx, int64_t dy, int64_t dz,
+                         VolumeBoxes vb, const float* __restrict__ xyz, float* __restrict__ out) {
+  const int64_t total = br.off[br.n];
+  for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x) {
+    const int b = brick_of_point(br, gi);
+    int c[3];
+    float w[3];
+    for (int d = 0; d < 3; ++d) {
+      const float x = fminf(fmaxf(xyz[3 * gi + d], -1.f), 1.f);
+      const int lo = vb.lo[b][d], hi = vb.hi[b][d];
+      const float s = fmaf((x + 1.f) * 0.5f, (float)(hi - lo), (float)lo);
+      const int ci = min(max((int)floorf(s), lo), hi - 1);
+      c[d] = ci;
+      w[d] = s - (float)ci;
+    }
+    const int64_t base = ((int64_t)c[2] * dy + c[1]) * dx + c[0];
+    const int64_t sy = dx, sz = dx * dy;
+    const float v0 = __ldg(vol + base), v1 = __ldg(vol + base + 1);
+    const float v2 = __ldg(vol + base + sy), v3 = __ldg(vol + base + sy + 1);
+    const float v4 = __ldg(vol + base + sz), v5 = __ldg(vol + base + sz + 1);
+    const float v6 = __ldg(vol + base + sz + sy), v7 = __ldg(vol + base + sz + sy + 1);
+    const float ax = 1.f - w[0], ay = 1.f - w[1], az = 1.f - w[2];
+    out[gi] = az * (ay * (ax * v0 + w[0] * v1) + w[1] * (ax * v2 + w[0] * v3)) +
+              w[2] * (ay * (ax * v4 + w[0] * v5) + w[1] * (ax * v6 + w[0] * v7));
+  }
+  (void)dz;
+}
+
+int blocks_for(int64_t n, int threads, int num_sms, int per_sm) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms * per_sm;
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, const TrainWs& ws,
+                           const float* xyz, float eps) {
+  const int64_t total = br.off[br.n];
+  if (total == 0) return cudaSuccess;
+  k_density_scalar<<<blocks_for(total, 256, L.num_sms, 8), 256, 0, L.stream>>>(br, ws, eps);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int tiles = 0;
+  for (int b = 0; b < br.n; ++b) tiles += (int)((br.off[b + 1] - br.off[b] + DT - 1) / DT);
+  const int grid = tiles < 2 * L.num_sms ? tiles : 2 * L.num_sms;
+  k_density_grad<<<grid, DNT, 0, L.stream>>>(md, br, ws, xyz, eps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Launch& L, const Bricks& br, const Model& md, const TrainWs& ws,
+                            bool density, float* dG, int64_t sdG, double* losses) {
+  k_finalize<<<br.n, kMaxGrids, 0, L.stream>>>(br, md, ws, density ? 1 : 0, dG, sdG, losses);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(const Launch& L, float* p, float* g, float* m, float* v, uint16_t* shadow,
+                        int64_t n_a, int64_t n_total, bool do_b, float lr_a, float lr_b,
+                        float beta1, float beta2, float eps, StepState* st) {
+  k_advance<<<1, 1, 0, L.stream>>>(st, do_b ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t n = (do_b ? n_total : n_a) / 4;
+  k_adam<<<blocks_for(n, 256, L.num_sms, 8), 256, 0, L.stream>>>(p, g, m, v, shadow, n_a, n_total,
+                                                                 do_b ? 1 : 0, lr_a, lr_b, beta1,
+                                                                 beta2, eps, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shadow(const Launch& L, const float* p, uint16_t* shadow, int64_t n) {
+  k_shadow<<<blocks_for(n / 4, 256, L.num_sms, 8), 256, 0, L.stream>>>(p, shadow, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const Launch& L, const Bricks& br, unsigned long long seed,
+                          unsigned long long step, const unsigned long long* step_dev,
+                          float* xyz, float* tmp, uint32_t* rank, uint32_t* hist) {
+  const int64_t total = br.off[br.n];
+  if (total == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kSortBins * br.n, L.stream);
+  if (e != cudaSuccess) return e;
+  const int blocks = blocks_for(total, 256, L.num_sms, 8);
+  k_sample_gen<<<blocks, 256, 0, L.stream>>>(br, seed, step, step_dev, tmp, rank, hist);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_sample_scan<<<br.n, 1024, 0, L.stream>>>(hist);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_sample_scatter<<<blocks, 256, 0, L.stream>>>(br, tmp, rank, hist, xyz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_target(const Launch& L, const Bricks& br, const float* vol, int64_t dx,
+                          int64_t dy, int64_t dz, const VolumeBoxes& vb, const float* xyz,
+                          float* target) {
+  const int64_t total = br.off[br.n];
+  if (total == 0) return cudaSuccess;
+  k_target<<<blocks_for(total, 256, L.num_sms, 8), 256, 0, L.stream>>>(br, vol, dx, dy, dz, vb, xyz, target);
+  return cudaGetLastError();
+}
+
+}  // namespace srn

@@ -1,0 +1,178 @@
+// Headless neural volume renderer (Sec. 6) over a domain decomposition (Sec. 5.3).
+//
+// Per batch of rays: (1) every (ray, sample) computes its position, its brick
+// through the spatial hash and its brick-local coordinate, and takes a rank in
+// its brick's bucket; (2) bucket offsets; (3) samples are scattered into brick
+// order; (4) the fused forward query runs over the buckets (device-side offsets);
+// (5) each ray gathers its values back in sample order and composites front to
+// back.  Sampling and opacity: midpoints t_j = t0 + (j + 1/2) dt of the ray's
+// segment inside [-1,1]^3, alpha = 1 - exp(-a dt / (2/512)), the 256-entry RGBA
+// transfer function read with linear interpolation.
+#include "common.cuh"
+#include "kernels.h"
+#include "render.h"
+
+namespace srn {
+namespace {
+
+struct Ray {
+  float ox, oy, oz, dx, dy, dz, t0, dt;
+  bool hit;
+};
+
+__device__ __forceinline__ Ray make_ray(const RenderParams& rp, int pix) {
+  const int px = pix % rp.width, py = pix / rp.width;
+  const float aspect = (float)rp.width / (float)rp.height;
+  const float nx = (2.f * ((float)px + 0.5f) / (float)rp.width - 1.f) * rp.cam.scale * aspect;
+  const float ny = (1.f - 2.f * ((float)py + 0.5f) / (float)rp.height) * rp.cam.scale;
+  Ray r;
+  const float* e = rp.cam.eye;
+  const float* f = rp.cam.forward;
+  const float* ri = rp.cam.right;
+  const float* u = rp.cam.up;
+  if (rp.cam.ortho) {
+    r.ox = e[0] + nx * ri[0] + ny * u[0];
+    r.oy = e[1] + nx * ri[1] + ny * u[1];
+    r.oz = e[2] + nx * ri[2] + ny * u[2];
+    r.dx = f[0]; r.dy = f[1]; r.dz = f[2];
+  } else {
+    r.ox = e[0]; r.oy = e[1]; r.oz = e[2];
+    float dx = f[0] + nx * ri[0] + ny * u[0];
+    float dy = f[1] + nx * ri[1] + ny * u[1];
+    float dz = f[2] + nx * ri[2] + ny * u[2];
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    r.dx = dx * inv; r.dy = dy * inv; r.dz = dz * inv;
+  }
+  // slab test against [-1, 1]^3
+  float tmin = -INFINITY, tmax = INFINITY;
+  const float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float inv = 1.f / d[a];
+    const float ta = (-1.f - o[a]) * inv, tb = (1.f - o[a]) * inv;
+    tmin = fmaxf(tmin, fminf(ta, tb));
+    tmax = fminf(tmax, fmaxf(ta, tb));
+  }
+  tmin = fmaxf(tmin, 0.f);
+  r.hit = tmax > tmin;
+  r.t0 = tmin;
+  r.dt = r.hit ? (tmax - tmin) / (float)rp.samples : 0.f;
+  return r;
+}
+
+__global__ void k_render_gen(RenderParams rp, int pix0, int npix, float* __restrict__ loc,
+                             uint32_t* __restrict__ rank, uint32_t* __restrict__ bid,
+                             uint32_t* __restrict__ cnt) {
+  const int64_t total = (int64_t)npix * rp.samples;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int ray = (int)(idx / rp.samples), j = (int)(idx % rp.samples);
+    const Ray r = make_ray(rp, pix0 + ray);
+    if (!r.hit) { bid[idx] = 0xffffffffu; continue; }
+    const float t = r.t0 + ((float)j + 0.5f) * r.dt;
+    const float p[3] = {r.ox + t * r.dx, r.oy + t * r.dy, r.oz + t * r.dz};
+    int cell[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {   // Sec. 5.3 hash, clamped to the brick grid
+      const int n = rp.grid[a];
+      cell[a] = min(max((int)floorf((float)n * (p[a] + 1.f) * 0.5f), 0), n - 1);
+    }
+    const int b = cell[0] + rp.grid[0] * (cell[1] + rp.grid[1] * cell[2]);
+    const float half = 0.5f * (float)(rp.vox - 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {   // global -> brick-local [-1, 1]
+      const float s = (p[a] + 1.f) * half;
+      const float lo = (float)rp.lo[b][a], hi = (float)rp.hi[b][a];
+      loc[3 * idx + a] = (s - lo) / (hi - lo) * 2.f - 1.f;
+    }
+    bid[idx] = (uint32_t)b;
+    rank[idx] = atomicAdd(cnt + b, 1u);
+  }
+}
+
+__global__ void k_render_offsets(int nb, const uint32_t* __restrict__ cnt, int64_t* __restrict__ off) {
+  if (threadIdx.x == 0) {
+    int64_t a = 0;
+    for (int b = 0; b < nb; ++b) { off[b] = a; a += cnt[b]; }
+    off[nb] = a;
+  }
+}
+
+__global__ void k_render_scatter(int64_t total, const float* __restrict__ loc, const uint32_t* __restrict__ rank,
+                                 const uint32_t* __restrict__ bid, const int64_t* __restrict__ off,
+                                 float* __restrict__ xyz, uint32_t* __restrict__ pos) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = bid[idx];
+    if (b == 0xffffffffu) continue;
+    const int64_t dst = off[b] + rank[idx];
+    xyz[3 * dst] = loc[3 * idx];
+    xyz[3 * dst + 1] = loc[3 * idx + 1];
+    xyz[3 * dst + 2] = loc[3 * idx + 2];
+    pos[idx] = (uint32_t)dst;
+  }
+}
+
+// One thread per ray: gather the ray's values in sample order and composite.
+__global__ void k_render_composite(RenderParams rp, int pix0, int npix, const uint32_t* __restrict__ pos,
+                                   const float* __restrict__ val, const float* __restrict__ lut,
+                                   float* __restrict__ rgba) {
+  const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ray >= npix) return;
+  const Ray r = make_ray(rp, pix0 + ray);
+  float cr = 0.f, cg = 0.f, cb = 0.f, T = 1.f;
+  if (r.hit) {
+    const float k = r.dt / (2.f / 512.f);
+    const float inv_span = 1.f / (rp.vmax - rp.vmin);
+    for (int j = 0; j < rp.samples; ++j) {
+      const float f = val[pos[(int64_t)ray * rp.samples + j]];
+      const float s = fminf(fmaxf((f - rp.vmin) * inv_span, 0.f), 1.f) * 255.f;
+      const int i0 = min((int)s, 254);
+      const float fr = s - (float)i0;
+      const float4 a = reinterpret_cast<const float4*>(lut)[i0];
+      const float4 c = reinterpret_cast<const float4*>(lut)[i0 + 1];
+      const float red = a.x + (c.x - a.x) * fr, grn = a.y + (c.y - a.y) * fr, blu = a.z + (c.z - a.z) * fr;
+      const float op = a.w + (c.w - a.w) * fr;
+      const float alpha = 1.f - expf(-op * k);
+      const float w = T * alpha;
+      cr = fmaf(w, red, cr); cg = fmaf(w, grn, cg); cb = fmaf(w, blu, cb);
+      T *= 1.f - alpha;
+    }
+  }
+  reinterpret_cast<float4*>(rgba)[pix0 + ray] = make_float4(cr, cg, cb, 1.f - T);
+}
+
+int blocks_for(int64_t n, int threads, int num_sms) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms * 8;
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_render_batch(const Launch& L, const RenderParams& rp, const RenderWs& w, int pix0,
+                                int npix, const Model& md, const float* lut, float* rgba) {
+  const int64_t total = (int64_t)npix * rp.samples;
+  const int nb = rp.grid[0] * rp.grid[1] * rp.grid[2];
+  cudaError_t e = cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nb, L.stream);
+  if (e != cudaSuccess) return e;
+  k_render_gen<<<blocks_for(total, 256, L.num_sms), 256, 0, L.stream>>>(rp, pix0, npix, w.loc, w.rank, w.bid, w.cnt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_render_offsets<<<1, 32, 0, L.stream>>>(nb, w.cnt, w.off);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_render_scatter<<<blocks_for(total, 256, L.num_sms), 256, 0, L.stream>>>(total, w.loc, w.rank, w.bid, w.off, w.xyz, w.pos);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  Bricks br{};
+  br.n = nb;
+  br.dev = w.off;
+  Grads gr{};
+  TrainWs tw{};
+  e = md.F16 ? launch_query_bf16(L, kForward, md, gr, br, tw, w.xyz, nullptr, w.val)
+             : launch_query_fp32(L, kForward, md, gr, br, tw, w.xyz, nullptr, w.val);
+  if (e != cudaSuccess) return e;
+  k_render_composite<<<(npix + 127) / 128, 128, 0, L.stream>>>(rp, pix0, npix, w.pos, w.val, lut, rgba);
+  return cudaGetLastError();
+}
+
+}  // namespace srn

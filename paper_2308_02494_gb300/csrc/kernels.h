@@ -1,0 +1,52 @@
+// Host-side launch wrappers of the libsrn kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace srn {
+
+enum QueryMode { kForward = 0, kTrain = 1, kTrainDensity = 2 };
+
+struct Launch {
+  cudaStream_t stream;
+  int num_sms;
+};
+
+// Fused encoder (Eq. 1-3) + decoder + (in training) L_rec backward, batched over bricks.
+cudaError_t launch_query_bf16(const Launch& L, QueryMode mode, const Model& md, const Grads& gr,
+                              const Bricks& br, const TrainWs& ws, const float* xyz,
+                              const float* target, float* out);
+cudaError_t launch_query_fp32(const Launch& L, QueryMode mode, const Model& md, const Grads& gr,
+                              const Bricks& br, const TrainWs& ws, const float* xyz,
+                              const float* target, float* out);
+
+// Density loss (Eq. 7-9) second and third passes, and the per-brick finalisation.
+cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, const TrainWs& ws,
+                           const float* xyz, float eps);
+cudaError_t launch_finalize(const Launch& L, const Bricks& br, const Model& md, const TrainWs& ws,
+                            bool density, float* dG, int64_t sdG, double* losses);
+
+// Adam over the flat parameter buffer; the step state lives in device memory.
+struct StepState {
+  unsigned long long step;   // sampler step (advanced once per srn_step)
+  int t_a, t_b;              // Adam step counts of group A (F, decoder) and B (G)
+};
+cudaError_t launch_adam(const Launch& L, float* p, float* g, float* m, float* v, uint16_t* shadow,
+                        int64_t n_a, int64_t n_total, bool do_b, float lr_a, float lr_b,
+                        float beta1, float beta2, float eps, StepState* st);
+cudaError_t launch_shadow(const Launch& L, const float* p, uint16_t* shadow, int64_t n);
+
+// Sampler (Philox + Morton counting sort) and ground-truth lookup.
+cudaError_t launch_sample(const Launch& L, const Bricks& br, unsigned long long seed,
+                          unsigned long long step, const unsigned long long* step_dev,
+                          float* xyz, float* tmp, uint32_t* rank, uint32_t* hist);
+struct VolumeBoxes {
+  int32_t lo[SRN_MAX_BRICKS][3];
+  int32_t hi[SRN_MAX_BRICKS][3];
+};
+cudaError_t launch_target(const Launch& L, const Bricks& br, const float* vol, int64_t dx,
+                          int64_t dy, int64_t dz, const VolumeBoxes& vb, const float* xyz,
+                          float* target);
+
+}  // namespace srn

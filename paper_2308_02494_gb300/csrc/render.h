@@ -1,0 +1,32 @@
+// Renderer launch parameters and workspace (internal to libsrn).
+#pragma once
+#include "common.cuh"
+#include "kernels.h"
+
+namespace srn {
+
+struct RenderParams {
+  srn_camera cam;
+  int32_t width, height, samples;
+  int32_t grid[3];
+  int64_t vox;
+  float vmin, vmax;
+  int32_t lo[SRN_MAX_BRICKS][3];
+  int32_t hi[SRN_MAX_BRICKS][3];
+};
+
+struct RenderWs {
+  float* loc;       // [max_points][3] brick-local sample coordinates, ray order
+  uint32_t* rank;   // [max_points] rank inside the brick bucket
+  uint32_t* bid;    // [max_points] brick of the sample (all ones: ray missed)
+  uint32_t* pos;    // [max_points] bucketed position of each sample
+  float* xyz;       // [max_points][3] bucketed coordinates
+  float* val;       // [max_points] queried values, bucketed order
+  uint32_t* cnt;    // [B] bucket sizes
+  int64_t* off;     // [B + 1] bucket offsets
+};
+
+cudaError_t launch_render_batch(const Launch& L, const RenderParams& rp, const RenderWs& w, int pix0,
+                                int npix, const Model& md, const float* lut, float* rgba);
+
+}  // namespace srn

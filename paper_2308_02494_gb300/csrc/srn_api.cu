@@ -1,0 +1,616 @@
+// C ABI of libsrn (declared in include/srn.h): argument validation, workspace
+// carving, kernel dispatch and the CUDA-graph cache of srn_train_step.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "render.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+srn_status fail(srn_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+srn_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(SRN_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+int64_t round64(int64_t n) { return (n + 63) / 64 * 64; }
+size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+srn_status check_config(const srn_config* c) {
+  if (!c) return fail(SRN_ERR_INVALID_ARG, "config is NULL");
+  if (c->n_bricks < 1 || c->n_bricks > SRN_MAX_BRICKS)
+    return fail(SRN_ERR_INVALID_ARG, "n_bricks %d outside [1, %d]", c->n_bricks, SRN_MAX_BRICKS);
+  if (c->n_grids < 1 || c->channels < 1 || c->res < 2 || c->hidden < 1)
+    return fail(SRN_ERR_INVALID_ARG, "non-positive model size");
+  if (c->hidden != srn::kHidden) return fail(SRN_ERR_UNSUPPORTED, "hidden must be 64");
+  if (c->channels > 2) return fail(SRN_ERR_UNSUPPORTED, "channels must be 1 or 2");
+  const int K = c->n_grids * c->channels;
+  if (K != 16 && K != 32 && K != 64 && K != 128)
+    return fail(SRN_ERR_UNSUPPORTED, "n_grids*channels = %d not in {16, 32, 64, 128}", K);
+  if (c->res > 64) return fail(SRN_ERR_UNSUPPORTED, "res %d > 64", c->res);
+  if (c->flat_top_p < 1 || c->flat_top_p > 16)
+    return fail(SRN_ERR_UNSUPPORTED, "flat_top_p %d outside [1, 16]", c->flat_top_p);
+  if (c->precision != SRN_FP32 && c->precision != SRN_BF16)
+    return fail(SRN_ERR_INVALID_ARG, "unknown precision %d", c->precision);
+  if (!(c->density_eps > 0.f) || !(c->lr_feat >= 0.f) || !(c->lr_xform >= 0.f) ||
+      !(c->beta1 >= 0.f && c->beta1 < 1.f) || !(c->beta2 >= 0.f && c->beta2 < 1.f) ||
+      !(c->adam_eps > 0.f))
+    return fail(SRN_ERR_INVALID_ARG, "bad optimiser or epsilon setting");
+  return SRN_OK;
+}
+
+void make_layout(const srn_config* c, srn_layout* L) {
+  const int64_t B = c->n_bricks, M = c->n_grids, R = c->res, C = c->channels;
+  const int64_t K = M * C;
+  L->size_F = round64(M * R * R * R * C);
+  L->size_W1 = round64(64 * K);
+  L->size_W2 = round64(64 * 64);
+  L->size_w3 = round64(64);
+  L->size_G = round64(M * 12);
+  L->off_F = 0;
+  L->off_W1 = L->off_F + B * L->size_F;
+  L->off_W2 = L->off_W1 + B * L->size_W1;
+  L->off_w3 = L->off_W2 + B * L->size_W2;
+  L->n_group_a = L->off_w3 + B * L->size_w3;
+  L->off_G = L->n_group_a;
+  L->n_params = L->off_G + B * L->size_G;
+}
+
+// Workspace carving (every piece 256-byte aligned).
+struct WsLayout {
+  size_t state, acc, gsum, rho, herr, sort_tmp, sort_rank, sort_hist;
+  size_t r_loc, r_rank, r_bid, r_pos, r_xyz, r_val, r_cnt, r_off, total;
+};
+
+WsLayout ws_layout(const srn_config* c, int64_t maxp) {
+  WsLayout w{};
+  size_t o = 0;
+  w.state = o; o += align256(sizeof(srn::StepState) + 64);
+  w.acc = o; o += align256(sizeof(double) * srn::kAccPerBrick * c->n_bricks);
+  w.gsum = o; o += align256(sizeof(double) * 13 * c->n_grids * c->n_bricks);
+  w.rho = o; o += align256(sizeof(float) * maxp);
+  w.herr = o; o += align256(sizeof(float) * maxp);
+  w.sort_tmp = o; o += align256(sizeof(float) * 3 * maxp);
+  w.sort_rank = o; o += align256(sizeof(uint32_t) * maxp);
+  w.sort_hist = o; o += align256(sizeof(uint32_t) * srn::kSortBins * c->n_bricks);
+  w.r_loc = o; o += align256(sizeof(float) * 3 * maxp);
+  w.r_rank = o; o += align256(sizeof(uint32_t) * maxp);
+  w.r_bid = o; o += align256(sizeof(uint32_t) * maxp);
+  w.r_pos = o; o += align256(sizeof(uint32_t) * maxp);
+  w.r_xyz = o; o += align256(sizeof(float) * 3 * maxp);
+  w.r_val = o; o += align256(sizeof(float) * maxp);
+  w.r_cnt = o; o += align256(sizeof(uint32_t) * c->n_bricks);
+  w.r_off = o; o += align256(sizeof(int64_t) * (c->n_bricks + 1));
+  w.total = o;
+  return w;
+}
+
+struct GraphKey {
+  uint32_t flags;
+  uint64_t seed;
+  const void* vol;
+  int64_t dims[3];
+  std::vector<int64_t> boxes, offsets;
+  const void *xyz, *target, *losses;
+  cudaStream_t stream;
+  bool operator==(const GraphKey& o) const {
+    return flags == o.flags && seed == o.seed && vol == o.vol && dims[0] == o.dims[0] &&
+           dims[1] == o.dims[1] && dims[2] == o.dims[2] && boxes == o.boxes &&
+           offsets == o.offsets && xyz == o.xyz && target == o.target && losses == o.losses &&
+           stream == o.stream;
+  }
+};
+
+struct GraphEntry {
+  GraphKey key;
+  int eager_runs;
+  cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct srn_handle {
+  srn_config cfg;
+  srn_layout lay;
+  srn_tensors t;
+  unsigned char* ws;
+  size_t ws_bytes;
+  int64_t max_points;
+  WsLayout wl;
+  int num_sms;
+  std::vector<GraphEntry> graphs;
+  // measurement hook: a ring of event pairs around the fused query kernel
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_start, ev_stop;
+  std::vector<char> ev_used;
+  size_t ev_next = 0;
+  double timed_ms = 0.0;
+  int64_t timed_launches = 0;
+
+  srn::StepState* state() const { return reinterpret_cast<srn::StepState*>(ws + wl.state); }
+  int32_t* status() const { return reinterpret_cast<int32_t*>(ws + wl.state + sizeof(srn::StepState)); }
+  srn::TrainWs train_ws() const {
+    srn::TrainWs w;
+    w.rho = reinterpret_cast<float*>(ws + wl.rho);
+    w.herr = reinterpret_cast<float*>(ws + wl.herr);
+    w.acc = reinterpret_cast<double*>(ws + wl.acc);
+    w.gsum = reinterpret_cast<double*>(ws + wl.gsum);
+    w.status = status();
+    w.upstream = 0;
+    return w;
+  }
+  srn::Model model() const {
+    srn::Model m{};
+    const float* p = t.params_dev;
+    const __nv_bfloat16* s = reinterpret_cast<const __nv_bfloat16*>(t.shadow_dev);
+    m.G = p + lay.off_G;
+    m.range = t.range_dev;
+    m.F32 = p + lay.off_F;
+    m.W1f = p + lay.off_W1;
+    m.W2f = p + lay.off_W2;
+    m.w3 = p + lay.off_w3;
+    m.F16 = s ? s + lay.off_F : nullptr;
+    m.W1h = s ? s + lay.off_W1 : nullptr;
+    m.W2h = s ? s + lay.off_W2 : nullptr;
+    m.sF = lay.size_F; m.sW1 = lay.size_W1; m.sW2 = lay.size_W2; m.sw3 = lay.size_w3; m.sG = lay.size_G;
+    m.M = cfg.n_grids; m.C = cfg.channels; m.R = cfg.res; m.K = cfg.n_grids * cfg.channels;
+    m.p = cfg.flat_top_p;
+    return m;
+  }
+  srn::Grads grads() const {
+    srn::Grads g{};
+    float* d = t.grads_dev;
+    g.dF = d + lay.off_F; g.dW1 = d + lay.off_W1; g.dW2 = d + lay.off_W2; g.dw3 = d + lay.off_w3;
+    g.sF = lay.size_F; g.sW1 = lay.size_W1; g.sW2 = lay.size_W2; g.sw3 = lay.size_w3;
+    return g;
+  }
+  srn::Launch launch(void* stream) const { return srn::Launch{static_cast<cudaStream_t>(stream), num_sms}; }
+};
+
+namespace {
+
+srn_status check_handle(const srn_handle* h) {
+  if (!h) return fail(SRN_ERR_INVALID_ARG, "handle is NULL");
+  return SRN_OK;
+}
+
+srn_status make_bricks(const srn_handle* h, const int64_t* offsets, srn::Bricks* br) {
+  if (!offsets) return fail(SRN_ERR_INVALID_ARG, "offsets is NULL");
+  const int B = h->cfg.n_bricks;
+  if (offsets[0] != 0) return fail(SRN_ERR_INVALID_ARG, "offsets[0] must be 0");
+  for (int b = 0; b < B; ++b)
+    if (offsets[b + 1] < offsets[b]) return fail(SRN_ERR_INVALID_ARG, "offsets decrease at brick %d", b);
+  if (offsets[B] > h->max_points)
+    return fail(SRN_ERR_INVALID_ARG, "%lld points exceed max_points %lld", (long long)offsets[B],
+                (long long)h->max_points);
+  br->n = B;
+  br->dev = nullptr;
+  for (int b = 0; b <= B; ++b) br->off[b] = offsets[b];
+  return SRN_OK;
+}
+
+srn_status check_training_counts(const srn::Bricks& br) {
+  for (int b = 0; b < br.n; ++b)
+    if (br.off[b + 1] == br.off[b])
+      return fail(SRN_ERR_INVALID_ARG, "brick %d has no points (its losses are means over the batch)", b);
+  return SRN_OK;
+}
+
+srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn::Bricks& br,
+                     const float* xyz, const float* target, float* out, int upstream = 0) {
+  const srn::Launch L = h->launch(stream);
+  const srn::Model md = h->model();
+  const srn::Grads gr = h->grads();
+  srn::TrainWs ws = h->train_ws();
+  ws.upstream = upstream;
+  size_t slot = 0;
+  bool timed = false;
+  if (h->timing && !h->ev_start.empty()) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(L.stream, &cap);
+    if (cap == cudaStreamCaptureStatusNone) {
+      slot = h->ev_next++ % h->ev_start.size();
+      if (h->ev_used[slot]) {  // retire the oldest pair before reusing it
+        float ms = 0.f;
+        cudaEventSynchronize(h->ev_stop[slot]);
+        cudaEventElapsedTime(&ms, h->ev_start[slot], h->ev_stop[slot]);
+        h->timed_ms += ms;
+        h->timed_launches += 1;
+        h->ev_used[slot] = 0;
+      }
+      cudaEventRecord(h->ev_start[slot], L.stream);
+      timed = true;
+    }
+  }
+  cudaError_t e = h->cfg.precision == SRN_BF16
+                      ? srn::launch_query_bf16(L, mode, md, gr, br, ws, xyz, target, out)
+                      : srn::launch_query_fp32(L, mode, md, gr, br, ws, xyz, target, out);
+  if (e != cudaSuccess) return cuda_fail(e, "query kernel");
+  if (timed) {
+    cudaEventRecord(h->ev_stop[slot], L.stream);
+    h->ev_used[slot] = 1;
+  }
+  return SRN_OK;
+}
+
+srn_status do_backward(srn_handle* h, void* stream, const float* xyz, const float* target,
+                       const srn::Bricks& br, uint32_t flags, double* losses) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool dens = (flags & SRN_DENSITY) != 0;
+  cudaError_t e = cudaMemsetAsync(h->t.grads_dev, 0, sizeof(float) * h->lay.n_params, s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->ws + h->wl.acc, 0, h->wl.gsum - h->wl.acc + sizeof(double) * 13 * h->cfg.n_grids * h->cfg.n_bricks, s);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  srn_status st = run_query(h, stream, dens ? srn::kTrainDensity : srn::kTrain, br, xyz, target,
+                            nullptr, (flags & SRN_UPSTREAM) ? 1 : 0);
+  if (st != SRN_OK) return st;
+  const srn::Launch L = h->launch(stream);
+  const srn::Model md = h->model();
+  if (dens) {
+    e = srn::launch_density(L, md, br, h->train_ws(), xyz, h->cfg.density_eps);
+    if (e != cudaSuccess) return cuda_fail(e, "density kernels");
+  }
+  e = srn::launch_finalize(L, br, md, h->train_ws(), dens, h->t.grads_dev + h->lay.off_G,
+                           h->lay.size_G, losses);
+  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
+  return SRN_OK;
+}
+
+srn_status do_step(srn_handle* h, void* stream, uint32_t flags) {
+  const srn_config& c = h->cfg;
+  cudaError_t e = srn::launch_adam(h->launch(stream), h->t.params_dev, h->t.grads_dev, h->t.adam_m_dev,
+                                   h->t.adam_v_dev, c.precision == SRN_BF16 ? h->t.shadow_dev : nullptr,
+                                   h->lay.n_group_a, h->lay.n_params, (flags & SRN_DENSITY) != 0,
+                                   c.lr_feat, c.lr_xform, c.beta1, c.beta2, c.adam_eps, h->state());
+  if (e != cudaSuccess) return cuda_fail(e, "adam kernel");
+  return SRN_OK;
+}
+
+srn_status make_boxes(const srn_handle* h, const int64_t dims[3], const int64_t* boxes,
+                      srn::VolumeBoxes* vb) {
+  if (!dims || !boxes) return fail(SRN_ERR_INVALID_ARG, "dims or boxes is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (dims[d] < 2) return fail(SRN_ERR_INVALID_ARG, "volume dimension %d < 2", d);
+  for (int b = 0; b < h->cfg.n_bricks; ++b) {
+    for (int d = 0; d < 3; ++d) {
+      const int64_t lo = boxes[6 * b + d], hi = boxes[6 * b + 3 + d];
+      if (lo < 0 || hi >= dims[d] || hi <= lo)
+        return fail(SRN_ERR_INVALID_ARG, "box of brick %d invalid on axis %d", b, d);
+      vb->lo[b][d] = (int32_t)lo;
+      vb->hi[b][d] = (int32_t)hi;
+    }
+  }
+  return SRN_OK;
+}
+
+srn_status enqueue_train_step(srn_handle* h, void* stream, uint64_t seed, const float* vol,
+                              const int64_t dims[3], const srn::VolumeBoxes& vb, const srn::Bricks& br,
+                              uint32_t flags, float* xyz, float* target, double* losses) {
+  const srn::Launch L = h->launch(stream);
+  unsigned char* ws = h->ws;
+  cudaError_t e = srn::launch_sample(L, br, seed, 0, &h->state()->step, xyz,
+                                     reinterpret_cast<float*>(ws + h->wl.sort_tmp),
+                                     reinterpret_cast<uint32_t*>(ws + h->wl.sort_rank),
+                                     reinterpret_cast<uint32_t*>(ws + h->wl.sort_hist));
+  if (e != cudaSuccess) return cuda_fail(e, "sampler");
+  e = srn::launch_target(L, br, vol, dims[0], dims[1], dims[2], vb, xyz, target);
+  if (e != cudaSuccess) return cuda_fail(e, "target lookup");
+  srn_status st = do_backward(h, stream, xyz, target, br, flags, losses);
+  if (st != SRN_OK) return st;
+  return do_step(h, stream, flags);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* srn_last_error(void) { return g_err.c_str(); }
+
+srn_status srn_param_layout(const srn_config* cfg, srn_layout* out) {
+  srn_status s = check_config(cfg);
+  if (s != SRN_OK) return s;
+  if (!out) return fail(SRN_ERR_INVALID_ARG, "out is NULL");
+  make_layout(cfg, out);
+  return SRN_OK;
+}
+
+srn_status srn_workspace_size(const srn_config* cfg, int64_t max_points, size_t* bytes) {
+  srn_status s = check_config(cfg);
+  if (s != SRN_OK) return s;
+  if (!bytes || max_points < 1) return fail(SRN_ERR_INVALID_ARG, "bytes is NULL or max_points < 1");
+  *bytes = ws_layout(cfg, max_points).total;
+  return SRN_OK;
+}
+
+srn_status srn_create(const srn_config* cfg, const srn_tensors* t, void* workspace, size_t ws_bytes,
+                      int64_t max_points, srn_handle** out) {
+  srn_status s = check_config(cfg);
+  if (s != SRN_OK) return s;
+  if (!t || !out || !workspace) return fail(SRN_ERR_INVALID_ARG, "tensors, workspace or out is NULL");
+  if (!t->params_dev || !t->grads_dev || !t->adam_m_dev || !t->adam_v_dev || !t->range_dev)
+    return fail(SRN_ERR_INVALID_ARG, "a required device tensor is NULL");
+  if (cfg->precision == SRN_BF16 && !t->shadow_dev)
+    return fail(SRN_ERR_INVALID_ARG, "BF16 precision needs the shadow buffer");
+  if (max_points < 1) return fail(SRN_ERR_INVALID_ARG, "max_points < 1");
+  const WsLayout wl = ws_layout(cfg, max_points);
+  if (ws_bytes < wl.total)
+    return fail(SRN_ERR_INVALID_ARG, "workspace of %zu bytes < %zu needed", ws_bytes, wl.total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+    return fail(SRN_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  for (const void* p : {(const void*)t->params_dev, (const void*)t->grads_dev, (const void*)t->adam_m_dev,
+                        (const void*)t->adam_v_dev, (const void*)t->shadow_dev})
+    if (reinterpret_cast<uintptr_t>(p) % 16 != 0)
+      return fail(SRN_ERR_INVALID_ARG, "tensor pointers must be 16-byte aligned");
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device query");
+  e = cudaMemset(static_cast<unsigned char*>(workspace) + wl.state, 0, wl.acc - wl.state);
+  if (e != cudaSuccess) return cuda_fail(e, "workspace init");
+  srn_handle* h = new srn_handle();
+  h->cfg = *cfg;
+  make_layout(cfg, &h->lay);
+  h->t = *t;
+  h->ws = static_cast<unsigned char*>(workspace);
+  h->ws_bytes = ws_bytes;
+  h->max_points = max_points;
+  h->wl = wl;
+  h->num_sms = sms;
+  *out = h;
+  return SRN_OK;
+}
+
+srn_status srn_destroy(srn_handle* h) {
+  if (!h) return fail(SRN_ERR_INVALID_ARG, "handle is NULL");
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (size_t i = 0; i < h->ev_start.size(); ++i) {
+    cudaEventDestroy(h->ev_start[i]);
+    cudaEventDestroy(h->ev_stop[i]);
+  }
+  delete h;
+  return SRN_OK;
+}
+
+srn_status srn_set_timing(srn_handle* h, int32_t enable) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (enable && h->ev_start.empty()) {
+    const int n = 256;
+    h->ev_start.resize(n);
+    h->ev_stop.resize(n);
+    h->ev_used.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+      cudaError_t e = cudaEventCreate(&h->ev_start[i]);
+      if (e == cudaSuccess) e = cudaEventCreate(&h->ev_stop[i]);
+      if (e != cudaSuccess) return cuda_fail(e, "event create");
+    }
+  }
+  std::fill(h->ev_used.begin(), h->ev_used.end(), 0);
+  h->ev_next = 0;
+  h->timed_ms = 0.0;
+  h->timed_launches = 0;
+  h->timing = enable != 0;
+  return SRN_OK;
+}
+
+srn_status srn_read_timing(srn_handle* h, double* total_ms, int64_t* launches) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (!total_ms || !launches) return fail(SRN_ERR_INVALID_ARG, "NULL output");
+  for (size_t i = 0; i < h->ev_used.size(); ++i) {
+    if (!h->ev_used[i]) continue;
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(h->ev_stop[i]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev_start[i], h->ev_stop[i]);
+    if (e != cudaSuccess) return cuda_fail(e, "event read");
+    h->timed_ms += ms;
+    h->timed_launches += 1;
+    h->ev_used[i] = 0;
+  }
+  *total_ms = h->timed_ms;
+  *launches = h->timed_launches;
+  h->timed_ms = 0.0;
+  h->timed_launches = 0;
+  return SRN_OK;
+}
+
+srn_status srn_sync_shadow(srn_handle* h, void* stream) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (h->cfg.precision != SRN_BF16) return SRN_OK;
+  cudaError_t e = srn::launch_shadow(h->launch(stream), h->t.params_dev, h->t.shadow_dev, h->lay.n_group_a);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "shadow kernel");
+}
+
+srn_status srn_sample_points(srn_handle* h, void* stream, uint64_t seed, uint64_t step,
+                             const uint64_t* step_dev, const int64_t* offsets, float* xyz) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  srn::Bricks br;
+  if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
+  if (!xyz) return fail(SRN_ERR_INVALID_ARG, "xyz is NULL");
+  cudaError_t e = srn::launch_sample(h->launch(stream), br, seed, step,
+                                     reinterpret_cast<const unsigned long long*>(step_dev), xyz,
+                                     reinterpret_cast<float*>(h->ws + h->wl.sort_tmp),
+                                     reinterpret_cast<uint32_t*>(h->ws + h->wl.sort_rank),
+                                     reinterpret_cast<uint32_t*>(h->ws + h->wl.sort_hist));
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "sampler");
+}
+
+srn_status srn_sample_target(srn_handle* h, void* stream, const float* vol, const int64_t dims[3],
+                             const int64_t* boxes, const float* xyz, const int64_t* offsets,
+                             float* target) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  srn::Bricks br;
+  srn::VolumeBoxes vb;
+  if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
+  if ((s = make_boxes(h, dims, boxes, &vb)) != SRN_OK) return s;
+  if (!vol || !xyz || !target) return fail(SRN_ERR_INVALID_ARG, "volume, xyz or target is NULL");
+  cudaError_t e = srn::launch_target(h->launch(stream), br, vol, dims[0], dims[1], dims[2], vb, xyz, target);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "target lookup");
+}
+
+srn_status srn_forward(srn_handle* h, void* stream, const float* xyz, const int64_t* offsets, float* out) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  srn::Bricks br;
+  if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
+  if (!xyz || !out) return fail(SRN_ERR_INVALID_ARG, "xyz or out is NULL");
+  return run_query(h, stream, srn::kForward, br, xyz, nullptr, out);
+}
+
+srn_status srn_backward(srn_handle* h, void* stream, const float* xyz, const float* target,
+                        const int64_t* offsets, uint32_t flags, double* losses) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  srn::Bricks br;
+  if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
+  if ((s = check_training_counts(br)) != SRN_OK) return s;
+  if (!xyz || !target) return fail(SRN_ERR_INVALID_ARG, "xyz or target is NULL");
+  if (flags & ~(SRN_DENSITY | SRN_UPSTREAM)) return fail(SRN_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  if ((flags & SRN_DENSITY) && (flags & SRN_UPSTREAM))
+    return fail(SRN_ERR_INVALID_ARG, "SRN_DENSITY needs the per-point error, which SRN_UPSTREAM lacks");
+  return do_backward(h, stream, xyz, target, br, flags, losses);
+}
+
+srn_status srn_step(srn_handle* h, void* stream, uint32_t flags) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (flags & ~SRN_DENSITY) return fail(SRN_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  return do_step(h, stream, flags);
+}
+
+srn_status srn_train_step(srn_handle* h, void* stream, uint64_t seed, const float* vol,
+                          const int64_t dims[3], const int64_t* boxes, const int64_t* offsets,
+                          uint32_t flags, float* xyz, float* target, double* losses) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  srn::Bricks br;
+  srn::VolumeBoxes vb;
+  if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
+  if ((s = check_training_counts(br)) != SRN_OK) return s;
+  if ((s = make_boxes(h, dims, boxes, &vb)) != SRN_OK) return s;
+  if (!vol || !xyz || !target) return fail(SRN_ERR_INVALID_ARG, "volume, xyz or target is NULL");
+  if (flags & ~SRN_DENSITY) return fail(SRN_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  if (stream == nullptr)
+    return enqueue_train_step(h, stream, seed, vol, dims, vb, br, flags, xyz, target, losses);
+
+  GraphKey key;
+  key.flags = flags; key.seed = seed; key.vol = vol;
+  for (int d = 0; d < 3; ++d) key.dims[d] = dims[d];
+  key.boxes.assign(boxes, boxes + 6 * h->cfg.n_bricks);
+  key.offsets.assign(offsets, offsets + h->cfg.n_bricks + 1);
+  key.xyz = xyz; key.target = target; key.losses = losses;
+  key.stream = static_cast<cudaStream_t>(stream);
+  GraphEntry* ge = nullptr;
+  for (auto& g : h->graphs)
+    if (g.key == key) ge = &g;
+  if (!ge) {
+    h->graphs.push_back(GraphEntry{key, 0, nullptr});
+    ge = &h->graphs.back();
+  }
+  if (!ge->exec) {
+    if (ge->eager_runs == 0) {  // first call: run eagerly (sets kernel attributes outside capture)
+      ge->eager_runs = 1;
+      return enqueue_train_step(h, stream, seed, vol, dims, vb, br, flags, xyz, target, losses);
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    s = enqueue_train_step(h, stream, seed, vol, dims, vb, br, flags, xyz, target, losses);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    if (s != SRN_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&ge->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ge->exec = nullptr;
+      return cuda_fail(e, "graph instantiate");
+    }
+  }
+  cudaError_t e = cudaGraphLaunch(ge->exec, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "graph launch");
+}
+
+srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const float* lut,
+                      float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
+                      const int32_t grid[3], const int64_t* boxes, int64_t vox, float* rgba) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (!cam || !lut || !grid || !boxes || !rgba) return fail(SRN_ERR_INVALID_ARG, "NULL argument");
+  if (width < 1 || height < 1 || samples < 1) return fail(SRN_ERR_INVALID_ARG, "empty image or no samples");
+  if ((int64_t)samples > h->max_points)
+    return fail(SRN_ERR_INVALID_ARG, "samples per ray %d exceed max_points", samples);
+  if (!(vmax > vmin)) return fail(SRN_ERR_INVALID_ARG, "vmax must exceed vmin");
+  if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1 || grid[0] * grid[1] * grid[2] != h->cfg.n_bricks)
+    return fail(SRN_ERR_INVALID_ARG, "brick grid does not match n_bricks");
+  if (vox < 2) return fail(SRN_ERR_INVALID_ARG, "vox < 2");
+  srn::RenderParams rp{};
+  rp.cam = *cam;
+  rp.width = width; rp.height = height; rp.samples = samples;
+  for (int a = 0; a < 3; ++a) rp.grid[a] = grid[a];
+  rp.vox = vox; rp.vmin = vmin; rp.vmax = vmax;
+  for (int b = 0; b < h->cfg.n_bricks; ++b)
+    for (int a = 0; a < 3; ++a) {
+      const int64_t lo = boxes[6 * b + a], hi = boxes[6 * b + 3 + a];
+      if (lo < 0 || hi >= vox || hi <= lo) return fail(SRN_ERR_INVALID_ARG, "box of brick %d invalid", b);
+      rp.lo[b][a] = (int32_t)lo; rp.hi[b][a] = (int32_t)hi;
+    }
+  unsigned char* ws = h->ws;
+  srn::RenderWs w;
+  w.loc = reinterpret_cast<float*>(ws + h->wl.r_loc);
+  w.rank = reinterpret_cast<uint32_t*>(ws + h->wl.r_rank);
+  w.bid = reinterpret_cast<uint32_t*>(ws + h->wl.r_bid);
+  w.pos = reinterpret_cast<uint32_t*>(ws + h->wl.r_pos);
+  w.xyz = reinterpret_cast<float*>(ws + h->wl.r_xyz);
+  w.val = reinterpret_cast<float*>(ws + h->wl.r_val);
+  w.cnt = reinterpret_cast<uint32_t*>(ws + h->wl.r_cnt);
+  w.off = reinterpret_cast<int64_t*>(ws + h->wl.r_off);
+  const int64_t npix = (int64_t)width * height;
+  const int64_t batch = h->max_points / samples;
+  const srn::Model md = h->model();
+  for (int64_t p0 = 0; p0 < npix; p0 += batch) {
+    const int n = (int)std::min<int64_t>(batch, npix - p0);
+    cudaError_t e = srn::launch_render_batch(h->launch(stream), rp, w, (int)p0, n, md, lut, rgba);
+    if (e != cudaSuccess) return cuda_fail(e, "render");
+  }
+  return SRN_OK;
+}
+
+srn_status srn_get_status(srn_handle* h, void* stream) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  int32_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, h->status(), sizeof v, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e == cudaSuccess && v) e = cudaMemsetAsync(h->status(), 0, sizeof v, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (v & 1) return fail(SRN_ERR_NONFINITE, "a loss was NaN or Inf");
+  return SRN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+"""Tensor-owning wrapper over the libsrn C ABI.
+
+``SRN`` allocates, with PyTorch, every device buffer the library needs (flat
+parameter / gradient / Adam buffers laid out by ``srn_param_layout``, the BF16
+shadow, the per-brick data range and the workspace), packs per-brick parameter
+dicts into the flat layout, and forwards calls to the entry points of
+``paper_2308_02494_gb300.srn``.  ``APMGSRNFunction`` puts the hand-written
+adjoint (``srn_backward`` with ``SRN_UPSTREAM``) behind ``torch.autograd``.
+All arithmetic runs in libsrn's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import srn as _s
+from .synth import ModelShape
+
+
+def _stream_ptr(stream) -> int:
+    return (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+
+
+class SRN:
+    def __init__(self, shape: ModelShape, n_bricks: int = 1, precision: str = "fp32",
+                 max_points: int = 1 << 18, device="cuda", flat_top_p: int = 10,
+                 density_eps: float = 1e-8, lr_feat: float = 1e-2, lr_xform: float = 1e-3,
+                 beta1: float = 0.9, beta2: float = 0.99, adam_eps: float = 1e-8):
+        self.shape = shape
+        self.n_bricks = n_bricks
+        self.device = torch.device(device)
+        self.bf16 = precision == "bf16"
+        self.cfg = _s.Config(n_bricks, shape.n_grids, shape.channels, shape.res, shape.hidden,
+                             _s.SRN_BF16 if self.bf16 else _s.SRN_FP32, flat_top_p, density_eps,
+                             lr_feat, lr_xform, beta1, beta2, adam_eps)
+        self.lay = _s.srn_param_layout(self.cfg)
+        n, na = self.lay.n_params, self.lay.n_group_a
+        kw = dict(device=self.device)
+        self.params = torch.zeros(n, dtype=torch.float32, **kw)
+        self.grads = torch.zeros(n, dtype=torch.float32, **kw)
+        self.adam_m = torch.zeros(n, dtype=torch.float32, **kw)
+        self.adam_v = torch.zeros(n, dtype=torch.float32, **kw)
+        self.shadow = torch.zeros(na, dtype=torch.int16, **kw) if self.bf16 else None
+        self.range = torch.zeros((n_bricks, 2), dtype=torch.float32, **kw)
+        self.range[:, 1] = 1.0
+        self.max_points = max_points
+        wsb = _s.srn_workspace_size(self.cfg, max_points)
+        self.workspace = torch.zeros(wsb + 256, dtype=torch.uint8, **kw)
+        ws_ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+        t = _s.Tensors(self.params.data_ptr(), self.grads.data_ptr(), self.adam_m.data_ptr(),
+                       self.adam_v.data_ptr(), self.shadow.data_ptr() if self.bf16 else None,
+                       self.range.data_ptr())
+        self.handle = _s.srn_create(self.cfg, t, ws_ptr, wsb, max_points)
+        self.losses = torch.zeros((n_bricks, 4), dtype=torch.float64, **kw)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                _s.srn_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    # ------------------------------------------------------------------ packing
+    def _views(self, flat: torch.Tensor, b: int) -> dict:
+        L, s = self.lay, self.shape
+        M, R, C, H, K = s.n_grids, s.res, s.channels, s.hidden, s.feat
+        return {
+            "F": flat[L.off_F + b * L.size_F: L.off_F + b * L.size_F + M * R ** 3 * C].view(M, R, R, R, C),
+            "W1": flat[L.off_W1 + b * L.size_W1: L.off_W1 + b * L.size_W1 + H * K].view(H, K),
+            "W2": flat[L.off_W2 + b * L.size_W2: L.off_W2 + b * L.size_W2 + H * H].view(H, H),
+            "w3": flat[L.off_w3 + b * L.size_w3: L.off_w3 + b * L.size_w3 + H],
+            "G": flat[L.off_G + b * L.size_G: L.off_G + b * L.size_G + M * 12].view(M, 3, 4),
+        }
+
+    def set_params(self, models, stream=None) -> None:
+        """models: one dict per brick (F, G, W1, W2, w3, vmin, vmax) of numpy arrays."""
+        if isinstance(models, dict):
+            models = [models]
+        assert len(models) == self.n_bricks
+        for b, m in enumerate(models):
+            v = self._views(self.params, b)
+            for k in ("F", "W1", "W2", "w3", "G"):
+                v[k].copy_(torch.as_tensor(np.asarray(m[k], dtype=np.float32)))
+            self.range[b, 0] = float(m["vmin"])
+            self.range[b, 1] = float(m["vmax"])
+        self.adam_m.zero_()
+        self.adam_v.zero_()
+        _s.srn_sync_shadow(self.handle, _stream_ptr(stream))
+
+    def get(self, which: str = "params") -> list:
+        flat = {"params": self.params, "grads": self.grads, "m": self.adam_m, "v": self.adam_v}[which]
+        out = []
+        for b in range(self.n_bricks):
+            d = {k: t.detach().cpu().numpy().astype(np.float64) for k, t in self._views(flat, b).items()}
+            d["vmin"], d["vmax"] = float(self.range[b, 0]), float(self.range[b, 1])
+            out.append(d)
+        return out
+
+    # ------------------------------------------------------------------ entry points
+    @staticmethod
+    def offsets_of(counts) -> list:
+        return [0] + list(np.cumsum([int(c) for c in counts]))
+
+    def forward(self, xyz: torch.Tensor, offsets, out: torch.Tensor | None = None, stream=None):
+        if out is None:
+            out = torch.empty(xyz.shape[0], dtype=torch.float32, device=self.device)
+        _s.srn_forward(self.handle, _stream_ptr(stream), xyz.data_ptr(), offsets, out.data_ptr())
+        return out
+
+    def backward(self, xyz, target, offsets, density: bool = False, upstream: bool = False, stream=None):
+        flags = (_s.SRN_DENSITY if density else 0) | (_s.SRN_UPSTREAM if upstream else 0)
+        _s.srn_backward(self.handle, _stream_ptr(stream), xyz.data_ptr(), target.data_ptr(), offsets,
+                        flags, self.losses.data_ptr())
+        return self.losses
+
+    def step(self, density: bool = False, stream=None) -> None:
+        _s.srn_step(self.handle, _stream_ptr(stream), _s.SRN_DENSITY if density else 0)
+
+    def sample_points(self, seed: int, step: int, offsets, xyz: torch.Tensor | None = None, stream=None):
+        if xyz is None:
+            xyz = torch.empty((offsets[-1], 3), dtype=torch.float32, device=self.device)
+        _s.srn_sample_points(self.handle, _stream_ptr(stream), seed, step, None, offsets, xyz.data_ptr())
+        return xyz
+
+    def sample_target(self, volume: torch.Tensor, boxes, xyz, offsets, target=None, stream=None):
+        if target is None:
+            target = torch.empty(xyz.shape[0], dtype=torch.float32, device=self.device)
+        dims = [volume.shape[2], volume.shape[1], volume.shape[0]]
+        _s.srn_sample_target(self.handle, _stream_ptr(stream), volume.data_ptr(), dims,
+                             np.asarray(boxes).ravel(), xyz.data_ptr(), offsets, target.data_ptr())
+        return target
+
+    def train_step(self, seed, volume, boxes, offsets, density, xyz, target, stream=None):
+        dims = [volume.shape[2], volume.shape[1], volume.shape[0]]
+        _s.srn_train_step(self.handle, _stream_ptr(stream), seed, volume.data_ptr(), dims,
+                          np.asarray(boxes).ravel(), offsets, _s.SRN_DENSITY if density else 0,
+                          xyz.data_ptr(), target.data_ptr(), self.losses.data_ptr())
+        return self.losses
+
+    def render(self, cam: dict, lut: torch.Tensor, vmin, vmax, width, height, samples, grid, boxes,
+               vox, rgba=None, stream=None):
+        if rgba is None:
+            rgba = torch.empty((height, width, 4), dtype=torch.float32, device=self.device)
+        c = _s.Camera((ct_f3(cam["eye"])), ct_f3(cam["forward"]), ct_f3(cam["right"]), ct_f3(cam["up"]),
+                      float(cam["scale"]), 1 if cam["ortho"] else 0)
+        _s.srn_render(self.handle, _stream_ptr(stream), c, lut.data_ptr(), vmin, vmax, width, height,
+                      samples, grid, np.asarray(boxes).ravel(), vox, rgba.data_ptr())
+        return rgba
+
+    def status(self, stream=None) -> None:
+        _s.srn_get_status(self.handle, _stream_ptr(stream))
+
+
+def ct_f3(v):
+    import ctypes as ct
+    return (ct.c_float * 3)(*[float(a) for a in v])
+
+
+class APMGSRNFunction(torch.autograd.Function):
+    """f = APMGSRN(x) with the flat parameter tensor as the differentiable input.
+
+    forward runs ``srn_forward``; backward runs ``srn_backward`` with
+    ``SRN_UPSTREAM`` (the incoming dL/df per point) and returns the flat
+    gradient for the parameters (no gradient for the coordinates)."""
+
+    @staticmethod
+    def forward(ctx, xyz, params, model: SRN, offsets):
+        ctx.model, ctx.offsets = model, offsets
+        ctx.save_for_backward(xyz)
+        return model.forward(xyz, offsets)
+
+    @staticmethod
+    def backward(ctx, grad_f):
+        (xyz,) = ctx.saved_tensors
+        g = grad_f.contiguous().to(torch.float32)
+        ctx.model.backward(xyz, g, ctx.offsets, upstream=True)
+        return None, ctx.model.grads.clone(), None, None

@@ -1,0 +1,191 @@
+"""Thin ctypes binding of libsrn (include/srn.h).
+
+Each function has the name of its C entry point and only marshals arguments:
+device pointers are passed as integers (e.g. ``tensor.data_ptr()``), streams as
+integers (``torch.cuda.Stream.cuda_stream``), host arrays as Python sequences.
+A non-OK status raises :class:`SrnError` with the library's message.  Nothing
+here computes any part of the model; if libsrn.so is missing, loading fails
+loudly (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsrn.so")
+
+SRN_OK = 0
+SRN_ERR_INVALID_ARG = 1
+SRN_ERR_UNSUPPORTED = 2
+SRN_ERR_CUDA = 3
+SRN_ERR_DEVICE_TIMEOUT = 4
+SRN_ERR_NONFINITE = 5
+SRN_ERR_STATE = 6
+SRN_FP32 = 0
+SRN_BF16 = 1
+SRN_DENSITY = 1
+SRN_UPSTREAM = 2
+SRN_MAX_BRICKS = 64
+
+# Every symbol include/srn.h declares (checked by the CPU tests).
+EXPORTS = (
+    "srn_param_layout", "srn_workspace_size", "srn_create", "srn_destroy", "srn_last_error",
+    "srn_sync_shadow", "srn_sample_points", "srn_sample_target", "srn_forward", "srn_backward",
+    "srn_step", "srn_train_step", "srn_render", "srn_set_timing", "srn_read_timing", "srn_get_status",
+)
+
+
+class SrnError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"libsrn status {status}: {message}")
+        self.status = status
+
+
+class Config(ct.Structure):
+    _fields_ = [("n_bricks", ct.c_int32), ("n_grids", ct.c_int32), ("channels", ct.c_int32),
+                ("res", ct.c_int32), ("hidden", ct.c_int32), ("precision", ct.c_int32),
+                ("flat_top_p", ct.c_int32), ("density_eps", ct.c_float), ("lr_feat", ct.c_float),
+                ("lr_xform", ct.c_float), ("beta1", ct.c_float), ("beta2", ct.c_float),
+                ("adam_eps", ct.c_float)]
+
+
+class Layout(ct.Structure):
+    _fields_ = [(n, ct.c_int64) for n in (
+        "n_params", "n_group_a", "off_F", "off_W1", "off_W2", "off_w3", "off_G",
+        "size_F", "size_W1", "size_W2", "size_w3", "size_G")]
+
+
+class Tensors(ct.Structure):
+    _fields_ = [("params_dev", ct.c_void_p), ("grads_dev", ct.c_void_p), ("adam_m_dev", ct.c_void_p),
+                ("adam_v_dev", ct.c_void_p), ("shadow_dev", ct.c_void_p), ("range_dev", ct.c_void_p)]
+
+
+class Camera(ct.Structure):
+    _fields_ = [("eye", ct.c_float * 3), ("forward", ct.c_float * 3), ("right", ct.c_float * 3),
+                ("up", ct.c_float * 3), ("scale", ct.c_float), ("ortho", ct.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ct.CDLL:
+    """Load libsrn.so once; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2308_02494_gb300.build`")
+    lib = ct.CDLL(path)
+    P, I64, I32, U64, U32, F = ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_uint64, ct.c_uint32, ct.c_float
+    I64P = ct.POINTER(ct.c_int64)
+    sig = {
+        "srn_param_layout": [ct.POINTER(Config), ct.POINTER(Layout)],
+        "srn_workspace_size": [ct.POINTER(Config), I64, ct.POINTER(ct.c_size_t)],
+        "srn_create": [ct.POINTER(Config), ct.POINTER(Tensors), P, ct.c_size_t, I64, ct.POINTER(P)],
+        "srn_destroy": [P],
+        "srn_sync_shadow": [P, P],
+        "srn_sample_points": [P, P, U64, U64, P, I64P, P],
+        "srn_sample_target": [P, P, P, I64P, I64P, P, I64P, P],
+        "srn_forward": [P, P, P, I64P, P],
+        "srn_backward": [P, P, P, P, I64P, U32, P],
+        "srn_step": [P, P, U32],
+        "srn_train_step": [P, P, U64, P, I64P, I64P, I64P, U32, P, P, P],
+        "srn_render": [P, P, ct.POINTER(Camera), P, F, F, I32, I32, I32, ct.POINTER(I32), I64P, I64, P],
+        "srn_get_status": [P, P],
+        "srn_set_timing": [P, I32],
+        "srn_read_timing": [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ct.c_int
+    lib.srn_last_error.argtypes = []
+    lib.srn_last_error.restype = ct.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st: int) -> None:
+    if st != SRN_OK:
+        raise SrnError(st, load().srn_last_error().decode())
+
+
+def _i64(seq) -> ct.Array:
+    vals = [int(v) for v in seq]
+    return (ct.c_int64 * len(vals))(*vals)
+
+
+def srn_last_error() -> str:
+    return load().srn_last_error().decode()
+
+
+def srn_param_layout(cfg: Config) -> Layout:
+    out = Layout()
+    _check(load().srn_param_layout(ct.byref(cfg), ct.byref(out)))
+    return out
+
+
+def srn_workspace_size(cfg: Config, max_points: int) -> int:
+    n = ct.c_size_t()
+    _check(load().srn_workspace_size(ct.byref(cfg), max_points, ct.byref(n)))
+    return n.value
+
+
+def srn_create(cfg: Config, tensors: Tensors, workspace: int, workspace_bytes: int, max_points: int) -> int:
+    h = ct.c_void_p()
+    _check(load().srn_create(ct.byref(cfg), ct.byref(tensors), workspace, workspace_bytes,
+                             max_points, ct.byref(h)))
+    return h.value
+
+
+def srn_destroy(h: int) -> None:
+    _check(load().srn_destroy(h))
+
+
+def srn_sync_shadow(h: int, stream: int) -> None:
+    _check(load().srn_sync_shadow(h, stream))
+
+
+def srn_sample_points(h, stream, seed, step, step_dev, offsets, xyz) -> None:
+    _check(load().srn_sample_points(h, stream, seed, step, step_dev, _i64(offsets), xyz))
+
+
+def srn_sample_target(h, stream, volume, dims, boxes, xyz, offsets, target) -> None:
+    _check(load().srn_sample_target(h, stream, volume, _i64(dims), _i64(boxes), xyz, _i64(offsets), target))
+
+
+def srn_forward(h, stream, xyz, offsets, out) -> None:
+    _check(load().srn_forward(h, stream, xyz, _i64(offsets), out))
+
+
+def srn_backward(h, stream, xyz, target, offsets, flags, losses) -> None:
+    _check(load().srn_backward(h, stream, xyz, target, _i64(offsets), flags, losses))
+
+
+def srn_step(h, stream, flags) -> None:
+    _check(load().srn_step(h, stream, flags))
+
+
+def srn_train_step(h, stream, seed, volume, dims, boxes, offsets, flags, xyz, target, losses) -> None:
+    _check(load().srn_train_step(h, stream, seed, volume, _i64(dims), _i64(boxes), _i64(offsets),
+                                 flags, xyz, target, losses))
+
+
+def srn_render(h, stream, cam: Camera, lut, vmin, vmax, width, height, samples, grid, boxes, vox, rgba) -> None:
+    g = (ct.c_int32 * 3)(*[int(v) for v in grid])
+    _check(load().srn_render(h, stream, ct.byref(cam), lut, vmin, vmax, width, height, samples, g,
+                             _i64(boxes), vox, rgba))
+
+
+def srn_set_timing(h, enable: bool) -> None:
+    _check(load().srn_set_timing(h, 1 if enable else 0))
+
+
+def srn_read_timing(h) -> tuple:
+    ms, n = ct.c_double(), ct.c_int64()
+    _check(load().srn_read_timing(h, ct.byref(ms), ct.byref(n)))
+    return ms.value, n.value
+
+
+def srn_get_status(h, stream) -> None:
+    _check(load().srn_get_status(h, stream))
