@@ -99,16 +99,40 @@ def relu(z):
     return np.maximum(z, 0.0)
 
 
-def mlp_forward(W1, W2, w3, y):
+def bf16(a):
+    """Round to the nearest bfloat16 (8 significant bits, ties to even), as float64.
+
+    Used only as the operand rounding of the mixed-precision reading: a bfloat16
+    number is a float32 whose low 16 bits are zero, so rounding keeps the high
+    half after adding half an ulp of the kept part (plus the kept lsb for ties)."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    bits = f.view(np.uint32).astype(np.uint64)
+    keep_lsb = (bits >> np.uint64(16)) & np.uint64(1)
+    bits = ((bits + np.uint64(0x7FFF) + keep_lsb) >> np.uint64(16)) << np.uint64(16)
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _ident(a):
+    return a
+
+
+def mlp_forward(W1, W2, w3, y, rnd=None):
     """Sec. 4.1.2: two bias-free hidden layers with ReLU, linear scalar output.
+
+    rnd (default none) rounds the activation operand of each hidden-layer matrix
+    product (y and ReLU(z1)); with rnd=bf16 this is the mixed-precision reading of
+    the decoder (BF16 operands, wide accumulation).  The weights are used as given.
     Returns (m [N], cache) with the pre-activations and activations."""
+    rnd = rnd or _ident
     W1, W2, w3 = (np.asarray(a, dtype=np.float64) for a in (W1, W2, w3))
-    z1 = y @ W1.T
+    yq = rnd(y)
+    z1 = yq @ W1.T
     h1 = relu(z1)
-    z2 = h1 @ W2.T
+    h1q = rnd(h1)
+    z2 = h1q @ W2.T
     h2 = relu(z2)
     m = h2 @ w3
-    return m, {"y": y, "z1": z1, "h1": h1, "z2": z2, "h2": h2}
+    return m, {"y": y, "yq": yq, "z1": z1, "h1": h1, "h1q": h1q, "z2": z2, "h2": h2}
 
 
 def scale_output(m, vmin, vmax):
@@ -116,10 +140,10 @@ def scale_output(m, vmin, vmax):
     return m * (vmax - vmin) + vmin
 
 
-def query(params: dict, x: np.ndarray) -> np.ndarray:
+def query(params: dict, x: np.ndarray, rnd=None) -> np.ndarray:
     """f(x) = d(e(x)): Eq. 1-3, the decoder and the output scaling.  Returns [N]."""
     y = encode(params["F"], params["G"], x)
-    m, _ = mlp_forward(params["W1"], params["W2"], params["w3"], y)
+    m, _ = mlp_forward(params["W1"], params["W2"], params["w3"], y, rnd)
     return scale_output(m, params["vmin"], params["vmax"])
 
 
@@ -189,12 +213,15 @@ def loss_density_fixed_target(G, x, rho_star, p: int = 10, eps: float = 1e-8) ->
 # ----------------------------------------------------------------------------- gradients
 
 
-def grad_rec(params: dict, x, v):
+def grad_rec(params: dict, x, v, rnd=None):
     """Analytic gradient of L_rec (Sec. 4.3.1) w.r.t. F, W1, W2, w3 (step (1) of
     Sec. 4.3.2: L_rec updates only the grids' features and the decoder).
 
     Chain rule written out: f = m (max-min) + min, dL/df = 2 (f - v)/N.
+    rnd (see mlp_forward) also rounds the activation-side operand of every
+    backward matrix product (dz2, dz1, and the y / ReLU(z1) factors of dW).
     Returns dict(L_rec, f, h, dF, dW1, dW2, dw3) where h = (f - v)^2 per point."""
+    q = rnd or _ident
     F = np.asarray(params["F"], dtype=np.float64)
     G = np.asarray(params["G"], dtype=np.float64)
     x = np.asarray(x, dtype=np.float64)
@@ -202,7 +229,7 @@ def grad_rec(params: dict, x, v):
     n = x.shape[0]
     M, R, C = F.shape[0], F.shape[1], F.shape[4]
     y = encode(F, G, x)
-    m, c = mlp_forward(params["W1"], params["W2"], params["w3"], y)
+    m, c = mlp_forward(params["W1"], params["W2"], params["w3"], y, rnd)
     span = params["vmax"] - params["vmin"]
     f = scale_output(m, params["vmin"], params["vmax"])
     r = f - v
@@ -211,10 +238,10 @@ def grad_rec(params: dict, x, v):
     W2 = np.asarray(params["W2"], dtype=np.float64)
     w3 = np.asarray(params["w3"], dtype=np.float64)
     dw3 = c["h2"].T @ dm
-    dz2 = dm[:, None] * w3[None, :] * (c["z2"] > 0)
-    dW2 = dz2.T @ c["h1"]
-    dz1 = (dz2 @ W2) * (c["z1"] > 0)
-    dW1 = dz1.T @ y
+    dz2 = q(dm[:, None] * w3[None, :] * (c["z2"] > 0))
+    dW2 = dz2.T @ c["h1q"]
+    dz1 = q((dz2 @ W2) * (c["z1"] > 0))
+    dW1 = dz1.T @ c["yq"]
     dy = dz1 @ W1                                     # [N, M*C]
     dF = np.zeros_like(F)
     u = local_coords(G, x)
@@ -223,9 +250,12 @@ def grad_rec(params: dict, x, v):
         ins = inside_mask(ui)
         cc, w = cell_and_weights(ui, R)
         g = dy[:, i * C:(i + 1) * C]
+        flat = dF[i].reshape(R * R * R, C)
         for dx, dyy, dz in corner_offsets():
             wt = (corner_weight(w, dx, dyy, dz) * ins)[:, None] * g
-            np.add.at(dF[i], (cc[:, 2] + dz, cc[:, 1] + dyy, cc[:, 0] + dx), wt)
+            node = ((cc[:, 2] + dz) * R + (cc[:, 1] + dyy)) * R + (cc[:, 0] + dx)
+            for ch in range(C):   # scatter-add of each point's share into its corner node
+                flat[:, ch] += np.bincount(node, weights=wt[:, ch], minlength=R * R * R)
     return {"L_rec": float(np.mean(r ** 2)), "f": f, "h": r ** 2, "dF": dF,
             "dW1": dW1, "dW2": dW2, "dw3": dw3}
 

@@ -99,15 +99,36 @@ __device__ __forceinline__ Cell make_cell(float ux, float uy, float uz, int R) {
   return c;
 }
 
+// x^E by repeated squaring (E known at compile time).
+template <int E>
+__device__ __forceinline__ float powi(float x) {
+  if constexpr (E == 0) {
+    return 1.f;
+  } else if constexpr (E == 1) {
+    return x;
+  } else if constexpr (E % 2 == 0) {
+    const float h = powi<E / 2>(x);
+    return h * h;
+  } else {
+    return x * powi<E - 1>(x);
+  }
+}
+
 // exp(-sum_d u_d^(2p)) of Eq. 7, and optionally 2p u_d^(2p-1) for its gradient.
 // Returns 0 (and zero derivatives) once the exponent passes 87, where the float32
-// exponential is below the smallest normal number.
+// exponential is below the smallest normal number.  p = 10 (the paper's value) takes
+// a fixed squaring chain; other p loop.
 __device__ __forceinline__ float flat_top(float ux, float uy, float uz, int p,
                                           float* dx = nullptr, float* dy = nullptr,
                                           float* dz = nullptr) {
   const float x2 = ux * ux, y2 = uy * uy, z2 = uz * uz;
-  float px = 1.f, py = 1.f, pz = 1.f;  // u^(2(p-1))
-  for (int k = 1; k < p; ++k) { px *= x2; py *= y2; pz *= z2; }
+  float px, py, pz;  // u^(2(p-1))
+  if (p == 10) {
+    px = powi<9>(x2); py = powi<9>(y2); pz = powi<9>(z2);
+  } else {
+    px = 1.f; py = 1.f; pz = 1.f;
+    for (int k = 1; k < p; ++k) { px *= x2; py *= y2; pz *= z2; }
+  }
   const float s = fmaf(px, x2, fmaf(py, y2, pz * z2));
   if (!(s <= 87.f)) {
     if (dx) { *dx = 0.f; *dy = 0.f; *dz = 0.f; }

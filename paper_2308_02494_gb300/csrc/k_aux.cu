@@ -30,34 +30,70 @@ __device__ __forceinline__ Tv warp_sum(Tv v) {
 // Per point: rho_s = rho/S, k = hbar/(h+eps), rho* = exp(k log(rho_s+eps)) (held
 // constant), g = dL/drho_s = -rho*/(N (rho_s+eps)).  Sums per brick:
 // c = sum g rho_s (needed by dL/drho = (g - c)/S) and L_den = mean rho* (k-1) log(rho_s+eps).
-__global__ void k_density_scalar(Bricks br, TrainWs ws, float eps) {
-  const int64_t total = br.off[br.n];
+// Per-point scalar chain of Eq. 8 in float32 (the terms whose rho* is not negligible
+// have |k log(rho_s + eps)| of order one, where float32 exp/log are accurate to a
+// few ulp); every sum is carried in float64.
+struct PointDensity {
+  float rs, k, lr, star, g;
+};
+__device__ __forceinline__ PointDensity point_density(float rho, float h, float invS, float hbar,
+                                                      float eps, float n) {
+  PointDensity d;
+  d.rs = rho * invS;
+  d.k = hbar / (h + eps);
+  d.lr = logf(d.rs + eps);
+  d.star = expf(d.k * d.lr);
+  d.g = -d.star / (n * (d.rs + eps));
+  return d;
+}
+
+constexpr int ST = 256;   // points per tile of the scalar pass
+
+__global__ void __launch_bounds__(ST) k_density_scalar(Bricks br, TrainWs ws, float eps) {
+  __shared__ TileMap tm;
+  __shared__ double red[2][ST / 32];
+  const int tid = threadIdx.x;
+  if (tid == 0) build_tile_map(br, ST, tm);
+  __syncthreads();
+  const int total = tm.first[br.n];
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int tb = blockIdx.x * per, te = min(total, tb + per);
   double c_acc = 0.0, l_acc = 0.0;
   int cur = -1;
-  for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ; gi += (int64_t)gridDim.x * blockDim.x) {
-    const bool live = gi < total;
-    const int b = live ? brick_of_point(br, gi) : -1;
-    // flush when the brick changes (warp-uniform flushes are not guaranteed, so
-    // each thread flushes its own partial with a float64 atomic)
-    if (b != cur) {
-      if (cur >= 0) {
-        atomicAdd(ws.acc + cur * kAccPerBrick + ACC_C, c_acc);
-        atomicAdd(ws.acc + cur * kAccPerBrick + ACC_LDEN, l_acc);
-      }
-      c_acc = 0.0; l_acc = 0.0; cur = b;
+  float invS = 0.f, hbar = 0.f, n = 1.f;
+  auto flush = [&](int b) {
+    c_acc = warp_sum(c_acc);
+    l_acc = warp_sum(l_acc);
+    if ((tid & 31) == 0) { red[0][tid >> 5] = c_acc; red[1][tid >> 5] = l_acc; }
+    __syncthreads();
+    if (tid == 0) {
+      double c = 0.0, l = 0.0;
+      for (int w = 0; w < ST / 32; ++w) { c += red[0][w]; l += red[1][w]; }
+      atomicAdd(ws.acc + b * kAccPerBrick + ACC_C, c);
+      atomicAdd(ws.acc + b * kAccPerBrick + ACC_LDEN, l);
     }
-    if (!live) break;
-    const double n = (double)(br.off[b + 1] - br.off[b]);
-    const double S = ws.acc[b * kAccPerBrick + ACC_SUM_RHO];
-    const double hbar = ws.acc[b * kAccPerBrick + ACC_SUM_R2] / n;
-    const double rs = (double)ws.rho[gi] / S;
-    const double k = hbar / ((double)ws.herr[gi] + (double)eps);
-    const double lr = log(rs + (double)eps);
-    const double star = exp(k * lr);
-    const double g = -star / (n * (rs + (double)eps));
-    c_acc += g * rs;
-    l_acc += star * (k - 1.0) * lr / n;
+    __syncthreads();
+    c_acc = 0.0;
+    l_acc = 0.0;
+  };
+  for (int tile = tb; tile < te; ++tile) {
+    const int b = brick_of_tile(tm, br.n, tile, cur);
+    if (b != cur) {
+      if (cur >= 0) flush(cur);
+      cur = b;
+      const double nb = (double)(br.off[b + 1] - br.off[b]);
+      n = (float)nb;
+      invS = (float)(1.0 / ws.acc[b * kAccPerBrick + ACC_SUM_RHO]);
+      hbar = (float)(ws.acc[b * kAccPerBrick + ACC_SUM_R2] / nb);
+    }
+    const int64_t p = br.off[b] + (int64_t)(tile - tm.first[b]) * ST + tid;
+    if (p < br.off[b + 1]) {
+      const PointDensity d = point_density(ws.rho[p], ws.herr[p], invS, hbar, eps, n);
+      c_acc += (double)d.g * (double)d.rs;
+      l_acc += (double)d.star * ((double)d.k - 1.0) * (double)d.lr / (double)n;
+    }
   }
+  if (cur >= 0) flush(cur);
 }
 
 // ------------------------------------------------------------ density pass 3
@@ -102,17 +138,18 @@ k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, f
   };
 
   int cur = -1;
-  double S = 1.0, hbar = 0.0, c = 0.0, n = 1.0;
+  float invS = 0.f, hbar = 0.f, c = 0.f, n = 1.f;
   for (int tile = tb; tile < te; ++tile) {
     const int b = brick_of_tile(tm, br.n, tile, cur);
     if (b != cur) {
       if (cur >= 0) flush(cur);
       cur = b;
       for (int k = tid; k < M * 12; k += DNT) sg[k] = md.G[(int64_t)b * md.sG + k];
-      n = (double)(br.off[b + 1] - br.off[b]);
-      S = ws.acc[b * kAccPerBrick + ACC_SUM_RHO];
-      hbar = ws.acc[b * kAccPerBrick + ACC_SUM_R2] / n;
-      c = ws.acc[b * kAccPerBrick + ACC_C];
+      const double nb = (double)(br.off[b + 1] - br.off[b]);
+      n = (float)nb;
+      invS = (float)(1.0 / ws.acc[b * kAccPerBrick + ACC_SUM_RHO]);
+      hbar = (float)(ws.acc[b * kAccPerBrick + ACC_SUM_R2] / nb);
+      c = (float)ws.acc[b * kAccPerBrick + ACC_C];
       __syncthreads();
     }
     const int64_t p0 = br.off[b] + (int64_t)(tile - tm.first[b]) * DT;
@@ -123,11 +160,8 @@ k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, f
       if (tid < np) {
         const int64_t gp = p0 + tid;
         v = make_float4(xyz[3 * gp], xyz[3 * gp + 1], xyz[3 * gp + 2], 0.f);
-        const double rs = (double)ws.rho[gp] / S;
-        const double k = hbar / ((double)ws.herr[gp] + (double)eps);
-        const double star = exp(k * log(rs + (double)eps));
-        const double g = -star / (n * (rs + (double)eps));
-        q = (float)((g - c) / S);
+        const PointDensity d = point_density(ws.rho[gp], ws.herr[gp], invS, hbar, eps, n);
+        q = (d.g - c) * invS;
       }
       sx[tid] = v;
       sq[tid] = q;
@@ -360,7 +394,10 @@ cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, c
                            const float* xyz, float eps) {
   const int64_t total = br.off[br.n];
   if (total == 0) return cudaSuccess;
-  k_density_scalar<<<blocks_for(total, 256, L.num_sms, 8), 256, 0, L.stream>>>(br, ws, eps);
+  int stiles = 0;
+  for (int b = 0; b < br.n; ++b) stiles += (int)((br.off[b + 1] - br.off[b] + ST - 1) / ST);
+  const int sgrid = stiles < 4 * L.num_sms ? stiles : 4 * L.num_sms;
+  k_density_scalar<<<sgrid, ST, 0, L.stream>>>(br, ws, eps);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int tiles = 0;

@@ -19,6 +19,13 @@
 #include "common.cuh"
 #include "kernels.h"
 
+// Phase markers (no-ops unless a profiling build defines them): SRN_PHASE_BEGIN at
+// kernel start, SRN_PHASE(k) after the block-wide barrier that ends phase k.
+#ifndef SRN_PHASE
+#define SRN_PHASE(k)
+#define SRN_PHASE_BEGIN
+#endif
+
 namespace srn {
 namespace {
 
@@ -125,8 +132,40 @@ struct Lay {
   static constexpr int RHO = X + T * 16;               // [2][T] f32 partial densities
   static constexpr int G = RHO + 2 * T * 4;            // [M][12] f32
   static constexpr int DET = G + kMaxGrids * 12 * 4;   // [M] f32
-  static constexpr int BYTES = DET + kMaxGrids * 4;
+  static constexpr int BOX = DET + kMaxGrids * 4;      // [M] TileBox
+  static constexpr int AABB = BOX + kMaxGrids * 32;    // [4][6] f32 per-warp partial bounds
+  static constexpr int BYTES = AABB + 4 * 6 * 4;
+  // During the encode, H1/DH2/DH1 (free until the decoder runs) hold each grid's
+  // staged node box; after the weight gradients, Y..DH1 hold the scatter scratch.
+  static constexpr int STG = H1;
+  static constexpr int STG_BYTES = 3 * T * 64 * 2;
+  static constexpr int SCR = Y;
+  static constexpr int SCR_WARP = ((T * K * 2 + STG_BYTES) / 8) / 16 * 16;  // per warp
 };
+
+// Node box of one grid covering one tile's points (from the tile's bounding box).
+struct TileBox {
+  int lo[3];      // first node (x, y, z)
+  int n[3];       // nodes per axis (cells per axis + 1); 0 when no point can be inside
+  int flags;      // bit 0: staged in shared memory, bit 1: scatter through the box
+  int cells;      // (n0 - 1)(n1 - 1)(n2 - 1)
+};
+enum { BOX_STAGED = 1, BOX_SCATTER = 2 };
+
+// Per-warp scatter scratch: per-cell corner sums, counting-sort arrays, point weights.
+template <int K>
+struct Scr {
+  static constexpr int FIX = T * 2 + T * 12 + T * 2 + 16;  // perm, weights, cell ids, slack
+  __host__ __device__ static constexpr int capc(int C) {
+    const int c = (Lay<K>::SCR_WARP - FIX) / (32 * C + 4);
+    return c > 256 ? 256 : c;
+  }
+};
+
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(g));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
 
 template <int K, int MODE>
 __global__ void __launch_bounds__(NT, 1)
@@ -145,6 +184,7 @@ k_query_bf16(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g8 = lane >> 2, t4 = lane & 3;
   const int M = md.M, C = md.C, R = md.R;
+  SRN_PHASE_BEGIN
   if (tid == 0) build_tile_map(br, T, tm);
   __syncthreads();
   const int total = tm.first[br.n];
@@ -246,21 +286,99 @@ k_query_bf16(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict
     const int64_t p0 = br.off[b] + (int64_t)(tile - tm.first[b]) * T;
     const int np = (int)min((int64_t)T, br.off[b + 1] - p0);
 
-    // ---- points (and targets) of the tile
+    // ---- points (and targets) of the tile, and per-warp partial bounding boxes
+    float* aabb = reinterpret_cast<float*>(sm + L::AABB);
+    TileBox* boxes = reinterpret_cast<TileBox*>(sm + L::BOX);
     if (tid < T) {
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (tid < np) {
+      const bool ok = tid < np;
+      if (ok) {
         const float* q = xyz + 3 * (p0 + tid);
         v.x = q[0]; v.y = q[1]; v.z = q[2];
         if (TRAIN) v.w = target[p0 + tid];
       }
       reinterpret_cast<float4*>(xs)[tid] = v;
+      float lo0 = ok ? v.x : INFINITY, lo1 = ok ? v.y : INFINITY, lo2 = ok ? v.z : INFINITY;
+      float hi0 = ok ? v.x : -INFINITY, hi1 = ok ? v.y : -INFINITY, hi2 = ok ? v.z : -INFINITY;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+        lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+        lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+        hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+        hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+        hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+      }
+      if (lane == 0) {
+        float* a = aabb + 6 * warp;
+        a[0] = lo0; a[1] = lo1; a[2] = lo2; a[3] = hi0; a[4] = hi1; a[5] = hi2;
+      }
     }
     __syncthreads();
+    SRN_PHASE(0);
 
-    // ---- encode: Eq. 1 and Eq. 2 for (point p, every other grid)
+    // ---- each grid's node box over the tile: the 8 corners of the tile's bounding
+    //      box mapped by Eq. 1, widened by 1e-3 cell so float32 rounding of any inner
+    //      point stays inside (every use below still bounds-checks the point's cell)
+    const int cap_nodes = L::STG_BYTES / (M * 2 * C);
+    const int capc = Scr<K>::capc(C);
+    if (tid < M) {
+      float lo[3], hi[3];
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = fminf(fminf(aabb[d], aabb[6 + d]), fminf(aabb[12 + d], aabb[18 + d]));
+        hi[d] = fmaxf(fmaxf(aabb[3 + d], aabb[9 + d]), fmaxf(aabb[15 + d], aabb[21 + d]));
+      }
+      float umin[3] = {INFINITY, INFINITY, INFINITY}, umax[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        float u[3];
+        affine(gs + 12 * tid, (k & 1) ? hi[0] : lo[0], (k & 2) ? hi[1] : lo[1], (k & 4) ? hi[2] : lo[2],
+               u[0], u[1], u[2]);
+        for (int d = 0; d < 3; ++d) { umin[d] = fminf(umin[d], u[d]); umax[d] = fmaxf(umax[d], u[d]); }
+      }
+      TileBox bx;
+      bool empty = np == 0;
+      const float h = 0.5f * (float)(R - 1);
+      for (int d = 0; d < 3; ++d) {
+        empty |= !(umax[d] >= -1.f - 1e-4f) || !(umin[d] <= 1.f + 1e-4f);
+        const float slo = (fmaxf(umin[d], -1.f) + 1.f) * h - 1e-3f;
+        const float shi = (fminf(umax[d], 1.f) + 1.f) * h + 1e-3f;
+        const int clo = min(max((int)floorf(slo), 0), R - 2);
+        const int chi = min(max((int)floorf(shi), 0), R - 2);
+        bx.lo[d] = clo;
+        bx.n[d] = chi - clo + 2;
+      }
+      if (empty) bx.n[0] = bx.n[1] = bx.n[2] = 0;
+      const int nodes = bx.n[0] * bx.n[1] * bx.n[2];
+      bx.cells = empty ? 0 : (bx.n[0] - 1) * (bx.n[1] - 1) * (bx.n[2] - 1);
+      bx.flags = (!empty && nodes <= cap_nodes && C == 2 ? BOX_STAGED : 0) |
+                 (!empty && bx.cells <= capc ? BOX_SCATTER : 0);
+      boxes[tid] = bx;
+    }
+    __syncthreads();
+    SRN_PHASE(1);
+
     const __nv_bfloat16* Fb = md.F16 + (int64_t)b * md.sF;
     const int64_t gsz = (int64_t)R * R * R * C;
+    // ---- stage each grid's node box (bf16 x 2 channels, 4 bytes a node) in shared
+    //      memory with asynchronous 4-byte copies, one box row per lane
+    for (int i = warp; i < M; i += NT / 32) {
+      const TileBox bx = boxes[i];
+      if (!(bx.flags & BOX_STAGED)) continue;
+      const uint32_t dst = su32(sm + L::STG) + (uint32_t)(i * cap_nodes * 4);
+      const unsigned int* src = reinterpret_cast<const unsigned int*>(Fb + i * gsz);
+      const int rows = bx.n[1] * bx.n[2];
+      for (int r = lane; r < rows; r += 32) {
+        const int qz = r / bx.n[1], qy = r - qz * bx.n[1];
+        const int64_t g0 = ((int64_t)(bx.lo[2] + qz) * R + (bx.lo[1] + qy)) * R + bx.lo[0];
+        for (int x = 0; x < bx.n[0]; ++x) cp_async4(dst + 4u * (uint32_t)(r * bx.n[0] + x), src + g0 + x);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    SRN_PHASE(2);
+
+    // ---- encode: Eq. 1 and Eq. 2 for (point p, every other grid)
     {
       const int p = (warp & 3) * 32 + lane, gsub = warp >> 2;
       const float4 pt = reinterpret_cast<const float4*>(xs)[p];
@@ -272,7 +390,27 @@ k_query_bf16(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict
         affine(gs + 12 * i, pt.x, pt.y, pt.z, ux, uy, uz);
         const Cell c = make_cell(ux, uy, uz, R);
         float f0 = 0.f, f1 = 0.f;
-        if (valid && c.inside) trilinear_bf16(Fb + i * gsz, c, R, C, f0, f1);
+        if (valid && c.inside) {
+          const TileBox& bx = boxes[i];
+          const int lx = c.cx - bx.lo[0], ly = c.cy - bx.lo[1], lz = c.cz - bx.lo[2];
+          if ((bx.flags & BOX_STAGED) && lx >= 0 && ly >= 0 && lz >= 0 && lx + 1 < bx.n[0] &&
+              ly + 1 < bx.n[1] && lz + 1 < bx.n[2]) {
+            const uint32_t* s = reinterpret_cast<const uint32_t*>(sm + L::STG) + i * cap_nodes;
+            const int sy = bx.n[0], sz = bx.n[0] * bx.n[1];
+            const int o = (lz * bx.n[1] + ly) * bx.n[0] + lx;
+            const float2 v0 = unpack_bf16(s[o]), v1 = unpack_bf16(s[o + 1]);
+            const float2 v2 = unpack_bf16(s[o + sy]), v3 = unpack_bf16(s[o + sy + 1]);
+            const float2 v4 = unpack_bf16(s[o + sz]), v5 = unpack_bf16(s[o + sz + 1]);
+            const float2 v6 = unpack_bf16(s[o + sz + sy]), v7 = unpack_bf16(s[o + sz + sy + 1]);
+            const float ax = 1.f - c.wx, ay = 1.f - c.wy, az = 1.f - c.wz;
+            f0 = az * (ay * (ax * v0.x + c.wx * v1.x) + c.wy * (ax * v2.x + c.wx * v3.x)) +
+                 c.wz * (ay * (ax * v4.x + c.wx * v5.x) + c.wy * (ax * v6.x + c.wx * v7.x));
+            f1 = az * (ay * (ax * v0.y + c.wx * v1.y) + c.wy * (ax * v2.y + c.wx * v3.y)) +
+                 c.wz * (ay * (ax * v4.y + c.wx * v5.y) + c.wy * (ax * v6.y + c.wx * v7.y));
+          } else {
+            trilinear_bf16(Fb + i * gsz, c, R, C, f0, f1);
+          }
+        }
         if (C == 2)
           *reinterpret_cast<uint32_t*>(sm + L::Y + swz<K>(p, 2 * i)) = pack_bf16(f0, f1);
         else
@@ -282,6 +420,7 @@ k_query_bf16(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict
       if (DENS) rhos[gsub * T + p] = rho;
     }
     __syncthreads();
+    SRN_PHASE(3);
     if (DENS && tid < np) {
       const float r = rhos[tid] + rhos[T + tid];
       ws.rho[p0 + tid] = r;
@@ -349,6 +488,7 @@ k_query_bf16(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict
         if (rhi < np) out[p0 + rhi] = fhi;
       }
       __syncthreads();
+      SRN_PHASE(4);
       continue;
     } else {
       // ---- L_rec and dL/dm = 2 (f - v) (max - min) / N
@@ -446,6 +586,7 @@ k_query_bf16(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict
         }
       }
       __syncthreads();
+      SRN_PHASE(4);
 
       // ---- dW2 += dz2^T H1 and dW1 += dz1^T Y over the tile's 128 points
       {
@@ -480,35 +621,162 @@ k_query_bf16(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict
         }
       }
 
-      // ---- scatter dL/dy into the gradient grids (adjoint of Eq. 2)
+      __syncthreads();  // Y..DH1 become the scatter scratch
+      SRN_PHASE(5);
+
+      // ---- scatter dL/dy into the gradient grids (adjoint of Eq. 2).  Warp w owns
+      //      grids w, w+8, ...: it counting-sorts the tile's points by their cell in
+      //      the grid's box (integer shared-memory atomics), sums each cell's eight
+      //      corner contributions with plain FMAs, then adds every box node into the
+      //      float32 gradient grid with one float2 atomic.  Points whose cell falls
+      //      outside a usable box add their corners directly.
       {
-        const int p = (warp & 3) * 32 + lane, gsub = warp >> 2;
-        if (p < np) {
-          const float4 pt = reinterpret_cast<const float4*>(xs)[p];
-          float* dFb = gr.dF + (int64_t)b * gr.sF;
-          for (int i = gsub; i < M; i += 2) {
-            float ux, uy, uz;
-            affine(gs + 12 * i, pt.x, pt.y, pt.z, ux, uy, uz);
-            const Cell c = make_cell(ux, uy, uz, R);
-            if (!c.inside) continue;
-            float g0, g1 = 0.f;
-            if (C == 2) {
-              const float2 g = *reinterpret_cast<const float2*>(dys + p * L::DYS + 2 * i);
-              g0 = g.x; g1 = g.y;
-            } else {
-              g0 = dys[p * L::DYS + i];
+        unsigned char* scr = sm + L::SCR + warp * L::SCR_WARP;
+        float* cs = reinterpret_cast<float*>(scr);                       // [capc][8C]
+        int* cnt = reinterpret_cast<int*>(scr + capc * 32 * C);          // [capc + 1]
+        unsigned short* perm = reinterpret_cast<unsigned short*>(cnt + capc + 1);  // [T]
+        float* wts = reinterpret_cast<float*>(scr + L::SCR_WARP - T * 12 - T * 2);  // [T][3]
+        short* cid = reinterpret_cast<short*>(scr + L::SCR_WARP - T * 2);          // [T]
+        float* dFb = gr.dF + (int64_t)b * gr.sF;
+        for (int i = warp; i < M; i += NT / 32) {
+          const TileBox bx = boxes[i];
+          float* dFi = dFb + i * gsz;
+          const bool boxed = (bx.flags & BOX_SCATTER) != 0;
+          const int cx = bx.n[0] - 1, cy = bx.n[1] - 1;
+          int rk[T / 32];
+          // (a) cell of each point in the box (or a direct scatter)
+#pragma unroll
+          for (int j = 0; j < T / 32; ++j) {
+            const int p = lane + 32 * j;
+            rk[j] = -1;
+            short id = -1;
+            if (p < np) {
+              const float4 pt = reinterpret_cast<const float4*>(xs)[p];
+              float ux, uy, uz;
+              affine(gs + 12 * i, pt.x, pt.y, pt.z, ux, uy, uz);
+              const Cell c = make_cell(ux, uy, uz, R);
+              float g0, g1 = 0.f;
+              if (C == 2) {
+                const float2 g = *reinterpret_cast<const float2*>(dys + p * L::DYS + 2 * i);
+                g0 = g.x; g1 = g.y;
+              } else {
+                g0 = dys[p * L::DYS + i];
+              }
+              if (c.inside && (g0 != 0.f || g1 != 0.f)) {
+                const int lx = c.cx - bx.lo[0], ly = c.cy - bx.lo[1], lz = c.cz - bx.lo[2];
+                if (boxed && lx >= 0 && ly >= 0 && lz >= 0 && lx < cx && ly < cy && lz < bx.n[2] - 1) {
+                  id = (short)((lz * cy + ly) * cx + lx);
+                  wts[3 * p] = c.wx; wts[3 * p + 1] = c.wy; wts[3 * p + 2] = c.wz;
+                } else {
+                  scatter_f32(dFi, c, R, C, g0, g1);
+                }
+              }
             }
-            if (g0 == 0.f && g1 == 0.f) continue;
-            scatter_f32(dFb + i * gsz, c, R, C, g0, g1);
+            if (p < T) cid[p] = id;
           }
+          if (!boxed) continue;  // warp-uniform
+          // (b) counting sort of the points by cell
+          for (int l = lane; l <= bx.cells; l += 32) cnt[l] = 0;
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < T / 32; ++j) {
+            const int id = cid[lane + 32 * j];
+            if (id >= 0) rk[j] = atomicAdd(cnt + id, 1);
+          }
+          __syncwarp();
+          {
+            const int per = (bx.cells + 31) / 32;
+            const int l0 = lane * per;
+            int run = 0;
+            for (int l = l0; l < min(l0 + per, bx.cells); ++l) run += cnt[l];
+            int incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int v = __shfl_up_sync(0xffffffffu, incl, o);
+              if (lane >= o) incl += v;
+            }
+            int acc = incl - run;
+            __syncwarp();
+            for (int l = l0; l < min(l0 + per, bx.cells); ++l) {
+              const int v = cnt[l];
+              cnt[l] = acc;
+              acc += v;
+            }
+            if (lane == 31) cnt[bx.cells] = incl;
+          }
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < T / 32; ++j) {
+            const int p = lane + 32 * j;
+            if (rk[j] >= 0) perm[cnt[cid[p]] + rk[j]] = (unsigned short)p;
+          }
+          __syncwarp();
+          // (c) per cell: the eight corner sums of its points
+          for (int l = lane; l < bx.cells; l += 32) {
+            float a[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) a[k] = 0.f;
+            for (int s = cnt[l]; s < cnt[l + 1]; ++s) {
+              const int p = perm[s];
+              const float wx = wts[3 * p], wy = wts[3 * p + 1], wz = wts[3 * p + 2];
+              const float ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
+              const float w[8] = {az * ay * ax, az * ay * wx, az * wy * ax, az * wy * wx,
+                                  wz * ay * ax, wz * ay * wx, wz * wy * ax, wz * wy * wx};
+              if (C == 2) {
+                const float2 g = *reinterpret_cast<const float2*>(dys + p * L::DYS + 2 * i);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) { a[2 * k] = fmaf(w[k], g.x, a[2 * k]); a[2 * k + 1] = fmaf(w[k], g.y, a[2 * k + 1]); }
+              } else {
+                const float g = dys[p * L::DYS + i];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) a[k] = fmaf(w[k], g, a[k]);
+              }
+            }
+            float* o = cs + l * 8 * C;
+            if (C == 2) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                reinterpret_cast<float4*>(o)[k] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+            } else {
+#pragma unroll
+              for (int k = 0; k < 2; ++k)
+                reinterpret_cast<float4*>(o)[k] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+            }
+          }
+          __syncwarp();
+          // (d) every node of the box gathers the corner sums of its (up to) 8 cells
+          const int rows = bx.n[1] * bx.n[2];
+          for (int r = lane; r < rows; r += 32) {
+            const int qz = r / bx.n[1], qy = r - qz * bx.n[1];
+            const int64_t g0 = ((int64_t)(bx.lo[2] + qz) * R + (bx.lo[1] + qy)) * R + bx.lo[0];
+            for (int qx = 0; qx < bx.n[0]; ++qx) {
+              float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                const int ex = qx - (k & 1), ey = qy - ((k >> 1) & 1), ez = qz - (k >> 2);
+                if (ex >= 0 && ey >= 0 && ez >= 0 && ex < cx && ey < cy && ez < bx.n[2] - 1) {
+                  const float* s = cs + ((ez * cy + ey) * cx + ex) * 8 * C + k * C;
+                  v0 += s[0];
+                  if (C == 2) v1 += s[1];
+                }
+              }
+              if (v0 != 0.f || v1 != 0.f) {
+                if (C == 2) atomicAdd(reinterpret_cast<float2*>(dFi) + g0 + qx, make_float2(v0, v1));
+                else atomicAdd(dFi + g0 + qx, v0);
+              }
+            }
+          }
+          __syncwarp();
         }
       }
       __syncthreads();
+      SRN_PHASE(6);
     }
   }
   if constexpr (TRAIN) {
     if (cur >= 0) flush(cur);
   }
+  SRN_PHASE(7);
 }
 
 template <int K, int MODE>

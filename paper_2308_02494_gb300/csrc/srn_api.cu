@@ -445,6 +445,7 @@ srn_status srn_sample_points(srn_handle* h, void* stream, uint64_t seed, uint64_
   if (s != SRN_OK) return s;
   srn::Bricks br;
   if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
+  if (br.off[br.n] == 0) return SRN_OK;
   if (!xyz) return fail(SRN_ERR_INVALID_ARG, "xyz is NULL");
   cudaError_t e = srn::launch_sample(h->launch(stream), br, seed, step,
                                      reinterpret_cast<const unsigned long long*>(step_dev), xyz,
@@ -463,6 +464,7 @@ srn_status srn_sample_target(srn_handle* h, void* stream, const float* vol, cons
   srn::VolumeBoxes vb;
   if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
   if ((s = make_boxes(h, dims, boxes, &vb)) != SRN_OK) return s;
+  if (br.off[br.n] == 0) return SRN_OK;
   if (!vol || !xyz || !target) return fail(SRN_ERR_INVALID_ARG, "volume, xyz or target is NULL");
   cudaError_t e = srn::launch_target(h->launch(stream), br, vol, dims[0], dims[1], dims[2], vb, xyz, target);
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "target lookup");
@@ -473,6 +475,7 @@ srn_status srn_forward(srn_handle* h, void* stream, const float* xyz, const int6
   if (s != SRN_OK) return s;
   srn::Bricks br;
   if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
+  if (br.off[br.n] == 0) return SRN_OK;  // nothing to query (empty tensors may have NULL data)
   if (!xyz || !out) return fail(SRN_ERR_INVALID_ARG, "xyz or out is NULL");
   return run_query(h, stream, srn::kForward, br, xyz, nullptr, out);
 }

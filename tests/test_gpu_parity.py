@@ -7,7 +7,8 @@ from oracle import apmgsrn as ap
 from oracle import render as orr
 from oracle import sampler as osp
 from paper_2308_02494_gb300 import synth
-from gpu_util import TOL, as_stored, ensure_built, make_model, points_off_faces, rel_l2
+from gpu_util import (EXACT, RND, TOL, as_stored, dG_error, density_grad_scale, ensure_built,
+                      make_model, morton_sorted, points_off_faces, points_off_kinks, rel_l2)
 
 pytestmark = pytest.mark.gpu
 
@@ -29,9 +30,23 @@ def _torch():
     return torch
 
 
-def _points_for(models, counts, seed):
-    xs = [points_off_faces(p["G"], n, seed + 7 * b) if n else np.zeros((0, 3), np.float32)
-          for b, (p, n) in enumerate(zip(models, counts))]
+def _points_for(models, counts, seed, rnd=None, layout="random"):
+    """Seeded points per brick, off every grid face and off every ReLU kink.
+
+    layout "random": uniform in [-1,1]^3, unordered (tiles span the domain, so the
+    kernel takes its per-corner path); "dense": uniform in a 0.3-wide cube and
+    Morton-ordered like the sampler's batches (tiles are compact, so the kernel
+    stages and scatters through its per-tile node boxes)."""
+    xs = []
+    for b, (p, n) in enumerate(zip(models, counts)):
+        if not n:
+            xs.append(np.zeros((0, 3), np.float32))
+            continue
+        lo, hi = (-1.0, 1.0) if layout == "random" else (-0.2 + 0.05 * b, 0.1 + 0.05 * b)
+        x = points_off_kinks(p, points_off_faces(p["G"], 2 * n + 64, seed + 7 * b, lo=lo, hi=hi), rnd)
+        assert len(x) >= n
+        x = x[:n]
+        xs.append(morton_sorted(x) if layout == "dense" else x)
     return xs
 
 
@@ -41,10 +56,12 @@ def test_forward_matches_oracle(shape, precision):
     torch = _torch()
     counts = [1000]
     m, ref = make_model(SHAPES[shape], 1, precision, 4096, seed=11)
-    x = _points_for(ref, counts, 3)[0]
+    x = _points_for(ref, counts, 3, RND[precision])[0]
     f = m.forward(torch.as_tensor(x, device="cuda"), [0, 1000]).cpu().numpy()
-    fo = ap.query(ref[0], x.astype(np.float64))
+    fo = ap.query(ref[0], x.astype(np.float64), rnd=RND[precision])
     assert rel_l2(f, fo) <= TOL[precision], rel_l2(f, fo)
+    fx = ap.query(ref[0], x.astype(np.float64))
+    assert rel_l2(f, fx) <= EXACT[precision]["value"], rel_l2(f, fx)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
@@ -52,12 +69,12 @@ def test_forward_uneven_bricks_with_an_empty_brick(precision):
     torch = _torch()
     counts = [0, 300, 7, 129]
     m, ref = make_model(SHAPES["m8r16c2"], 4, precision, 1024, seed=12)
-    xs = _points_for(ref, counts, 4)
+    xs = _points_for(ref, counts, 4, RND[precision])
     off = m.offsets_of(counts)
     f = m.forward(torch.as_tensor(np.concatenate(xs), device="cuda"), off).cpu().numpy()
     for b in range(4):
         if counts[b]:
-            fo = ap.query(ref[b], xs[b].astype(np.float64))
+            fo = ap.query(ref[b], xs[b].astype(np.float64), rnd=RND[precision])
             assert rel_l2(f[off[b]:off[b + 1]], fo) <= TOL[precision], b
 
 
@@ -70,8 +87,8 @@ def test_forward_of_nothing_is_a_no_op():
     assert torch.all(out == 7.0)
 
 
-def _oracle_backward(ref, x, v, density):
-    g = ap.grad_rec(ref, x.astype(np.float64), v.astype(np.float64))
+def _oracle_backward(ref, x, v, density, rnd=None):
+    g = ap.grad_rec(ref, x.astype(np.float64), v.astype(np.float64), rnd=rnd)
     out = dict(g)
     if density:
         d = ap.grad_density(ref["G"], x.astype(np.float64), g["h"])
@@ -79,34 +96,44 @@ def _oracle_backward(ref, x, v, density):
     return out
 
 
+@pytest.mark.parametrize("layout", ["random", "dense"])
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
-@pytest.mark.parametrize("shape", ["m8r16c2", "m16r9c1", "m64r32c2"])
-def test_backward_matches_oracle(shape, precision):
+@pytest.mark.parametrize("shape", ["m8r16c2", "m16r9c1", "m32r20c2", "m64r32c2"])
+def test_backward_matches_oracle(shape, precision, layout):
     torch = _torch()
     n = 1500
     m, ref = make_model(SHAPES[shape], 1, precision, 4096, seed=21)
-    x = _points_for(ref, [n], 5)[0]
+    x = _points_for(ref, [n], 5, RND[precision], layout)[0]
     v = np.random.default_rng(6).uniform(-0.5, 1.5, n).astype(np.float32)
     losses = m.backward(torch.as_tensor(x, device="cuda"), torch.as_tensor(v, device="cuda"),
                         [0, n], density=True).cpu().numpy()
     gr = m.get("grads")[0]
-    o = _oracle_backward(ref[0], x, v, True)
+    o = _oracle_backward(ref[0], x, v, True, RND[precision])
     tol = TOL[precision]
     assert abs(losses[0, 0] - o["L_rec"]) <= tol * abs(o["L_rec"])
     assert abs(losses[0, 1] - o["L_den"]) <= tol * abs(o["L_den"]) + 1e-12
     assert abs(losses[0, 2] - o["S"]) <= tol * o["S"]
     assert losses[0, 3] == n
-    for k, ok in (("F", "dF"), ("W1", "dW1"), ("W2", "dW2"), ("w3", "dw3"), ("G", "dG")):
+    for k, ok in (("F", "dF"), ("W1", "dW1"), ("W2", "dW2"), ("w3", "dw3")):
         e = rel_l2(gr[k], o[ok])
         assert e <= tol, (k, e)
+    scale = density_grad_scale(ref[0]["G"], x, o["h"])
+    assert dG_error(gr["G"], o["dG"], scale) <= tol, dG_error(gr["G"], o["dG"], scale)
+    if precision == "bf16":   # against the exact (unrounded) oracle: the stated looser bounds
+        ox = _oracle_backward(ref[0], x, v, True)
+        assert abs(losses[0, 0] - ox["L_rec"]) <= EXACT["bf16"]["value"] * ox["L_rec"]
+        for k, ok in (("F", "dF"), ("W1", "dW1"), ("W2", "dW2"), ("w3", "dw3")):
+            assert rel_l2(gr[k], ox[ok]) <= EXACT["bf16"]["grad"], (k, rel_l2(gr[k], ox[ok]))
+        assert dG_error(gr["G"], ox["dG"], scale) <= EXACT["bf16"]["grad"]
 
 
+@pytest.mark.parametrize("layout", ["random", "dense"])
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_backward_uneven_bricks(precision):
+def test_backward_uneven_bricks(precision, layout):
     torch = _torch()
     counts = [257, 31, 140]
     m, ref = make_model(SHAPES["m8r16c2"], 3, precision, 1024, seed=22)
-    xs = _points_for(ref, counts, 8)
+    xs = _points_for(ref, counts, 8, RND[precision], layout)
     r = np.random.default_rng(9)
     vs = [r.uniform(0, 1, c).astype(np.float32) for c in counts]
     off = m.offsets_of(counts)
@@ -115,11 +142,13 @@ def test_backward_uneven_bricks(precision):
     grads = m.get("grads")
     tol = TOL[precision]
     for b in range(3):
-        o = _oracle_backward(ref[b], xs[b], vs[b], True)
+        o = _oracle_backward(ref[b], xs[b], vs[b], True, RND[precision])
         assert abs(losses[b, 0] - o["L_rec"]) <= tol * o["L_rec"], b
         assert abs(losses[b, 1] - o["L_den"]) <= tol * abs(o["L_den"]) + 1e-12, b
-        for k, ok in (("F", "dF"), ("W1", "dW1"), ("W2", "dW2"), ("w3", "dw3"), ("G", "dG")):
+        for k, ok in (("F", "dF"), ("W1", "dW1"), ("W2", "dW2"), ("w3", "dw3")):
             assert rel_l2(grads[b][k], o[ok]) <= tol, (b, k, rel_l2(grads[b][k], o[ok]))
+        scale = density_grad_scale(ref[b]["G"], xs[b], o["h"])
+        assert dG_error(grads[b]["G"], o["dG"], scale) <= tol, b
 
 
 def test_backward_without_density_leaves_G_gradient_zero_and_rejects_empty_bricks():

@@ -63,3 +63,30 @@ def test_adam_constant_gradient_keeps_unit_steps():
         p_new, m, v = ap.adam_update(p, g, m, v, t, lr=1e-3)
         np.testing.assert_allclose(p_new - p, -1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-9)
         p = p_new
+
+
+def test_bf16_rounding_closed_form():
+    # bfloat16 keeps 8 significant bits; halfway cases go to the even neighbour.
+    from oracle.apmgsrn import bf16
+    vals = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -7, -2.5, 3.14159265, 0.0,
+                     1 + 2 ** -8 + 2 ** -20, 255.5])
+    want = np.array([1.0, 1.0, 1 + 2 ** -6, 1 + 2 ** -7, -2.5, 3.140625, 0.0,
+                     1 + 2 ** -7, 256.0])
+    np.testing.assert_array_equal(bf16(vals), want)
+    tiny = bf16(np.array([1e-30]))[0]
+    assert tiny != 0.0 and abs(tiny - 1e-30) <= 2 ** -8 * 1e-30
+
+
+def test_bf16_operand_rounding_only_touches_activations():
+    # With operands already representable in bfloat16 the rounded decoder is the exact one.
+    from oracle.apmgsrn import bf16
+    r = np.random.default_rng(3)
+    y = bf16(r.normal(size=(5, 8)))
+    W1, W2, w3 = r.normal(size=(4, 8)), np.eye(4), r.normal(size=4)
+    W1 = bf16(W1)
+    m_exact, c = ap.mlp_forward(W1, W2, w3, y)
+    m_rnd, _ = ap.mlp_forward(W1, W2, w3, y, rnd=bf16)
+    # h1 is rounded in the second product: equal iff h1 is representable
+    same = np.all(bf16(c["h1"]) == c["h1"], axis=1)
+    np.testing.assert_array_equal(m_rnd[same], m_exact[same])
+    assert not np.allclose(m_rnd, m_exact, rtol=1e-12, atol=0) or np.all(same)
