@@ -61,6 +61,8 @@ struct TrainWs {
   double* gsum;     // [B][M][13] float64 sums for dL_den/dG
   int32_t* status;  // device status word
   int32_t upstream; // 1: the target slot holds dL/df (no L_rec); 0: MSE against targets
+  __nv_bfloat16* Y;   // [N][K] features (BF16 training pass)
+  __nv_bfloat16* dY;  // [M][N][C] dL/dy, grid-major (BF16 training pass)
 };
 // Per-brick float64 accumulator slots.
 enum { ACC_SUM_R2 = 0, ACC_SUM_RHO = 1, ACC_C = 2, ACC_LDEN = 3, kAccPerBrick = 4 };
@@ -181,6 +183,21 @@ __device__ __forceinline__ void build_tile_map(const Bricks& br, int T, TileMap&
   for (int b = 0; b < br.n; ++b) {
     tm.first[b] = acc;
     acc += (int)((br.off[b + 1] - br.off[b] + T - 1) / T);
+  }
+  tm.first[br.n] = acc;
+}
+
+// Per-brick tile sizes (a launch whose tiles should cover similar volumes in every
+// brick, whatever its point density).
+struct TileSizes {
+  int32_t t[SRN_MAX_BRICKS];
+};
+
+__device__ __forceinline__ void build_tile_map_sized(const Bricks& br, const TileSizes& ts, TileMap& tm) {
+  int acc = 0;
+  for (int b = 0; b < br.n; ++b) {
+    tm.first[b] = acc;
+    acc += (int)((br.off[b + 1] - br.off[b] + ts.t[b] - 1) / ts.t[b]);
   }
   tm.first[br.n] = acc;
 }

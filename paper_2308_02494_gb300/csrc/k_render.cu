@@ -168,7 +168,7 @@ cudaError_t launch_render_batch(const Launch& L, const RenderParams& rp, const R
   br.dev = w.off;
   Grads gr{};
   TrainWs tw{};
-  e = md.F16 ? launch_query_bf16(L, kForward, md, gr, br, tw, w.xyz, nullptr, w.val)
+  e = md.F16 ? launch_forward_bf16(L, md, br, w.xyz, w.val)
              : launch_query_fp32(L, kForward, md, gr, br, tw, w.xyz, nullptr, w.val);
   if (e != cudaSuccess) return e;
   k_render_composite<<<(npix + 127) / 128, 128, 0, L.stream>>>(rp, pix0, npix, w.pos, w.val, lut, rgba);

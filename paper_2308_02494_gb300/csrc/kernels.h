@@ -13,10 +13,13 @@ struct Launch {
   int num_sms;
 };
 
-// Fused encoder (Eq. 1-3) + decoder + (in training) L_rec backward, batched over bricks.
-cudaError_t launch_query_bf16(const Launch& L, QueryMode mode, const Model& md, const Grads& gr,
-                              const Bricks& br, const TrainWs& ws, const float* xyz,
-                              const float* target, float* out);
+// BF16 path: fused forward query, and the three-kernel training pass (encoder,
+// decoder forward/backward, scatter), batched over bricks.
+cudaError_t launch_forward_bf16(const Launch& L, const Model& md, const Bricks& br, const float* xyz,
+                                float* out);
+cudaError_t launch_train_bf16(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
+                              const TrainWs& ws, const float* xyz, const float* target);
+// FP32 path: one fused kernel per mode (encoder + SIMT decoder + per-corner scatter).
 cudaError_t launch_query_fp32(const Launch& L, QueryMode mode, const Model& md, const Grads& gr,
                               const Bricks& br, const TrainWs& ws, const float* xyz,
                               const float* target, float* out);

@@ -74,7 +74,7 @@ void make_layout(const srn_config* c, srn_layout* L) {
 
 // Workspace carving (every piece 256-byte aligned).
 struct WsLayout {
-  size_t state, acc, gsum, rho, herr, sort_tmp, sort_rank, sort_hist;
+  size_t state, acc, gsum, rho, herr, sort_tmp, sort_rank, sort_hist, feat, dfeat;
   size_t r_loc, r_rank, r_bid, r_pos, r_xyz, r_val, r_cnt, r_off, total;
 };
 
@@ -89,6 +89,10 @@ WsLayout ws_layout(const srn_config* c, int64_t maxp) {
   w.sort_tmp = o; o += align256(sizeof(float) * 3 * maxp);
   w.sort_rank = o; o += align256(sizeof(uint32_t) * maxp);
   w.sort_hist = o; o += align256(sizeof(uint32_t) * srn::kSortBins * c->n_bricks);
+  // BF16 training pass: features Y [N][K] and dL/dy [M][N][C], both bfloat16
+  const size_t kbytes = c->precision == SRN_BF16 ? sizeof(uint16_t) * c->n_grids * c->channels : 0;
+  w.feat = o; o += align256(kbytes * maxp);
+  w.dfeat = o; o += align256(kbytes * maxp);
   w.r_loc = o; o += align256(sizeof(float) * 3 * maxp);
   w.r_rank = o; o += align256(sizeof(uint32_t) * maxp);
   w.r_bid = o; o += align256(sizeof(uint32_t) * maxp);
@@ -153,6 +157,8 @@ struct srn_handle {
     w.gsum = reinterpret_cast<double*>(ws + wl.gsum);
     w.status = status();
     w.upstream = 0;
+    w.Y = reinterpret_cast<__nv_bfloat16*>(ws + wl.feat);
+    w.dY = reinterpret_cast<__nv_bfloat16*>(ws + wl.dfeat);
     return w;
   }
   srn::Model model() const {
@@ -238,9 +244,13 @@ srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn
       timed = true;
     }
   }
-  cudaError_t e = h->cfg.precision == SRN_BF16
-                      ? srn::launch_query_bf16(L, mode, md, gr, br, ws, xyz, target, out)
-                      : srn::launch_query_fp32(L, mode, md, gr, br, ws, xyz, target, out);
+  cudaError_t e;
+  if (h->cfg.precision != SRN_BF16)
+    e = srn::launch_query_fp32(L, mode, md, gr, br, ws, xyz, target, out);
+  else if (mode == srn::kForward)
+    e = srn::launch_forward_bf16(L, md, br, xyz, out);
+  else
+    e = srn::launch_train_bf16(L, mode == srn::kTrainDensity, md, gr, br, ws, xyz, target);
   if (e != cudaSuccess) return cuda_fail(e, "query kernel");
   if (timed) {
     cudaEventRecord(h->ev_stop[slot], L.stream);
