@@ -134,6 +134,28 @@ srn_status srn_sync_shadow(srn_handle* h, void* stream);
 srn_status srn_sample_points(srn_handle* h, void* stream, uint64_t seed, uint64_t step,
                              const uint64_t* step_dev, const int64_t* offsets, float* xyz_dev);
 
+/* Allocation-free variant of srn_sample_points (the paper has no counterpart; this is
+ * an interface convenience).  Some callers cannot allocate device memory at all -- a
+ * plug-in running inside a host application that owns the GPU memory budget, or a
+ * real-time loop whose allocator must not be entered -- so they cannot create a handle
+ * with its workspace.  This entry point needs neither: its scratch (the unsorted draws,
+ * each point's rank in its bin, and the bin histograms) is a file-scope __device__
+ * array of 3 MiB that every GPU which loads the library holds until the process
+ * exits.  It calls no allocation routine of any kind.
+ *   - At most SRN_STATIC_SAMPLER_MAX_POINTS points over at most
+ *     SRN_STATIC_SAMPLER_MAX_BRICKS bricks; larger requests return SRN_ERR_INVALID_ARG.
+ *   - Same draws and same per-brick Morton ordering as srn_sample_points with
+ *     step_dev = NULL (order inside a bin may differ between runs).
+ *   - The first call on a device looks up that device's copy of the array (with the
+ *     device current); make that first call before any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (two streams, or two
+ *     host threads) race on it and must be serialised by the caller.  The histograms
+ *     are cleared on the stream at the start of every call. */
+#define SRN_STATIC_SAMPLER_MAX_POINTS 131072
+#define SRN_STATIC_SAMPLER_MAX_BRICKS 8
+srn_status srn_sample_points_static(void* stream, uint64_t seed, uint64_t step, int32_t n_bricks,
+                                    const int64_t* offsets, float* xyz_dev);
+
 /* Ground truth v(x) of Sec. 4.3.1: trilinear interpolation of a float32 volume
  * [dims[2]][dims[1]][dims[0]] (x fastest).  Brick b's local [-1,1]^3 spans the
  * inclusive voxel box boxes[b] = (lo_x, lo_y, lo_z, hi_x, hi_y, hi_z) (host

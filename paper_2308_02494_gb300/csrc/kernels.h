@@ -52,4 +52,7 @@ cudaError_t launch_target(const Launch& L, const Bricks& br, const float* vol, i
                           int64_t dy, int64_t dz, const VolumeBoxes& vb, const float* xyz,
                           float* target);
 
+// Sets the calling thread's srn_last_error() message and returns s.
+srn_status report(srn_status s, const char* message);
+
 }  // namespace srn

@@ -29,6 +29,13 @@ srn_status cuda_fail(cudaError_t e, const char* where) {
   return fail(SRN_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+}  // namespace
+
+// Entry points defined in other translation units report through this.
+srn_status srn::report(srn_status s, const char* message) { return fail(s, "%s", message); }
+
+namespace {
+
 int64_t round64(int64_t n) { return (n + 63) / 64 * 64; }
 size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 

@@ -32,7 +32,10 @@ EXPORTS = (
     "srn_param_layout", "srn_workspace_size", "srn_create", "srn_destroy", "srn_last_error",
     "srn_sync_shadow", "srn_sample_points", "srn_sample_target", "srn_forward", "srn_backward",
     "srn_step", "srn_train_step", "srn_render", "srn_set_timing", "srn_read_timing", "srn_get_status",
+    "srn_sample_points_static",
 )
+SRN_STATIC_SAMPLER_MAX_POINTS = 131072
+SRN_STATIC_SAMPLER_MAX_BRICKS = 8
 
 
 class SrnError(RuntimeError):
@@ -94,6 +97,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
         "srn_get_status": [P, P],
         "srn_set_timing": [P, I32],
         "srn_read_timing": [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)],
+        "srn_sample_points_static": [P, U64, U64, I32, I64P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -185,6 +189,11 @@ def srn_read_timing(h) -> tuple:
     ms, n = ct.c_double(), ct.c_int64()
     _check(load().srn_read_timing(h, ct.byref(ms), ct.byref(n)))
     return ms.value, n.value
+
+
+def srn_sample_points_static(stream, seed, step, n_bricks, offsets, xyz) -> None:
+    """Batch sampler that allocates nothing (scratch in a static device array)."""
+    _check(load().srn_sample_points_static(stream, seed, step, n_bricks, _i64(offsets), xyz))
 
 
 def srn_get_status(h, stream) -> None:
