@@ -204,13 +204,23 @@ srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const 
                       float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
                       const int32_t grid[3], const int64_t* boxes, int64_t vox, float* rgba_dev);
 
-/* Measurement hook (no counterpart in the paper).  While enabled, every launch of
- * the fused query kernel (srn_forward / srn_backward, also inside srn_train_step
- * when it runs eagerly) outside stream capture is bracketed by CUDA events on its
- * stream.  srn_read_timing synchronises on the recorded events and returns the
- * summed kernel time in milliseconds and the number of launches since the last
- * read (then resets both).  Enabling or disabling clears the counters. */
-srn_status srn_set_timing(srn_handle* h, int32_t enable);
+/* Measurement hook (no counterpart in the paper).  `target` picks what is timed:
+ * SRN_TIME_OFF nothing; SRN_TIME_QUERY every launch of the query pass (srn_forward,
+ * srn_backward, and srn_train_step when it runs eagerly: the fused kernel, or the
+ * three kernels of the BF16 training pass together); SRN_TIME_ENCODER,
+ * SRN_TIME_DECODER or SRN_TIME_SCATTER one kernel of the BF16 training pass
+ * (srn_backward of a BF16 handle; other calls are not timed).  Launches made outside
+ * stream capture are bracketed by CUDA events on their stream.  srn_read_timing
+ * synchronises on the recorded events and returns the summed kernel time in
+ * milliseconds and the number of timed launches since the last read (then resets
+ * both).  Changing the target clears the counters.  Any other target is
+ * SRN_ERR_INVALID_ARG. */
+#define SRN_TIME_OFF 0
+#define SRN_TIME_QUERY 1
+#define SRN_TIME_ENCODER 2
+#define SRN_TIME_DECODER 3
+#define SRN_TIME_SCATTER 4
+srn_status srn_set_timing(srn_handle* h, int32_t target);
 srn_status srn_read_timing(srn_handle* h, double* total_ms, int64_t* launches);
 
 /* Synchronise `stream` and report device-side status: SRN_ERR_NONFINITE if a loss

@@ -15,6 +15,8 @@ constexpr int kMaxK = 128;
 constexpr int kMaxGrids = 128;
 constexpr int kSortBits = 5;                       // 32^3 Morton bins per brick
 constexpr int kSortBins = 1 << (3 * kSortBits);
+constexpr int kUnitBits = kSortBits - 1;          // a unit is 2 x 2 x 2 bins
+constexpr int kUnits = 1 << (3 * kUnitBits);
 
 // Per-launch description of the bricks: points of brick b are [off[b], off[b+1]).
 // When `dev` is non-NULL the offsets are read from device memory at kernel start
@@ -63,6 +65,18 @@ struct TrainWs {
   int32_t upstream; // 1: the target slot holds dL/df (no L_rec); 0: MSE against targets
   __nv_bfloat16* Y;   // [N][K] features (BF16 training pass)
   __nv_bfloat16* dY;  // [M][N][C] dL/dy, grid-major (BF16 training pass)
+  int32_t* ustart;    // [B][kUnits + 1] first point of each Morton unit (BF16 scatter tiles)
+  struct ScatTile* tiles;  // scatter tiles (BF16 training pass)
+  int32_t* tile_ctr;  // [0] tiles written, [1] next tile to take
+};
+
+// A scatter tile: `count` (<= 1024) consecutive points of one brick, all in the aligned
+// Morton range of 2^L units starting at unit u0 when the brick's points are sorted by
+// Morton bin.  code = brick << 20 | L << 16 | u0.
+struct ScatTile {
+  int64_t start;
+  int32_t count;
+  uint32_t code;
 };
 // Per-brick float64 accumulator slots.
 enum { ACC_SUM_R2 = 0, ACC_SUM_RHO = 1, ACC_C = 2, ACC_LDEN = 3, kAccPerBrick = 4 };
@@ -160,6 +174,33 @@ __device__ __forceinline__ float2 unpack_bf16(uint32_t v) {
   return __bfloat1622float2(b);
 }
 
+// ------------------------------------------------------------------ Morton order
+// Morton code of the batch sampler's bins: bit 3k is bit k of the x bin, bit 3k+1 of
+// the y bin, bit 3k+2 of the z bin, with 2^kSortBits bins per axis over [-1, 1].
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 10 bits -> every third bit
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0xff0000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__device__ __forceinline__ uint32_t compact3(uint32_t v) {  // every third bit -> 10 bits
+  v &= 0x09249249u;
+  v = (v ^ (v >> 2)) & 0x030c30c3u;
+  v = (v ^ (v >> 4)) & 0x0300f00fu;
+  v = (v ^ (v >> 8)) & 0xff0000ffu;
+  v = (v ^ (v >> 16)) & 0x000003ffu;
+  return v;
+}
+__device__ __forceinline__ uint32_t morton_bin(float x, float y, float z) {
+  const float s = (float)(1 << kSortBits) * 0.5f;
+  const uint32_t ix = (uint32_t)min(max((int)((x + 1.f) * s), 0), (1 << kSortBits) - 1);
+  const uint32_t iy = (uint32_t)min(max((int)((y + 1.f) * s), 0), (1 << kSortBits) - 1);
+  const uint32_t iz = (uint32_t)min(max((int)((z + 1.f) * s), 0), (1 << kSortBits) - 1);
+  return spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+}
+
 // ------------------------------------------------------------------ Philox4x32-10
 __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
 #pragma unroll
@@ -183,21 +224,6 @@ __device__ __forceinline__ void build_tile_map(const Bricks& br, int T, TileMap&
   for (int b = 0; b < br.n; ++b) {
     tm.first[b] = acc;
     acc += (int)((br.off[b + 1] - br.off[b] + T - 1) / T);
-  }
-  tm.first[br.n] = acc;
-}
-
-// Per-brick tile sizes (a launch whose tiles should cover similar volumes in every
-// brick, whatever its point density).
-struct TileSizes {
-  int32_t t[SRN_MAX_BRICKS];
-};
-
-__device__ __forceinline__ void build_tile_map_sized(const Bricks& br, const TileSizes& ts, TileMap& tm) {
-  int acc = 0;
-  for (int b = 0; b < br.n; ++b) {
-    tm.first[b] = acc;
-    acc += (int)((br.off[b + 1] - br.off[b] + ts.t[b] - 1) / ts.t[b]);
   }
   tm.first[br.n] = acc;
 }

@@ -286,21 +286,6 @@ __global__ void k_shadow(const float* __restrict__ p, uint16_t* __restrict__ sha
 }
 
 // ------------------------------------------------------------ sampler
-__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 5 bits -> every third bit
-  v &= 0x1f;
-  v = (v | (v << 8)) & 0x0300F00Fu;
-  v = (v | (v << 4)) & 0x030C30C3u;
-  v = (v | (v << 2)) & 0x09249249u;
-  return v;
-}
-__device__ __forceinline__ uint32_t morton_bin(float x, float y, float z) {
-  const float s = (float)(1 << kSortBits) * 0.5f;
-  const uint32_t ix = (uint32_t)min((int)((x + 1.f) * s), (1 << kSortBits) - 1);
-  const uint32_t iy = (uint32_t)min((int)((y + 1.f) * s), (1 << kSortBits) - 1);
-  const uint32_t iz = (uint32_t)min((int)((z + 1.f) * s), (1 << kSortBits) - 1);
-  return spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
-}
-
 __global__ void k_sample_gen(Bricks br, unsigned long long seed, unsigned long long step,
                              const unsigned long long* step_dev, float* tmp, uint32_t* rank,
                              uint32_t* hist) {

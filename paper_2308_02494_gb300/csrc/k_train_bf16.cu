@@ -7,19 +7,24 @@
 //          BF16 operands, FP32 accumulation): L_rec partial sums, h(x) = (f - v)^2,
 //          dW1/dW2/dw3 accumulated in registers per CTA and flushed once, and
 //          dL/dy written grid-major as bf16 (dY [M][N][C]) for the scatter.
-//  k_scat  adjoint of Eq. 2.  A tile is 1024 Morton-consecutive points of one brick.
-//          The CTA takes the grids one at a time: it counting-sorts the tile's points
-//          by their cell in the grid's node box (integer shared-memory atomics, a
-//          block-wide scan), sums each cell's eight corner contributions with plain
-//          FMAs into corner-major per-cell sums, and lets every node of the box gather
-//          its (up to) eight cells and add the total into the float32 gradient grid
-//          with one float2 atomic.  The box is the exact bounding box of the cells the
-//          tile's points occupy in that grid; when it exceeds the shared-memory
-//          capacity the tile falls back to a box per 256-point chunk, then to adding
-//          each point's corners directly.
+//  k_scat  adjoint of Eq. 2.  A tile is up to 1024 points of one brick lying in one
+//          aligned Morton range of the sampler's bins (a small axis-aligned block of
+//          the brick), listed by k_unit_starts / k_tile_list.  The CTA takes the grids
+//          one at a time: the tile's block, mapped through the grid's Eq. 1, bounds
+//          the node box; the CTA counting-sorts the tile's points by their cell in that
+//          box (integer shared-memory atomics, a block-wide scan), sums each cell's
+//          eight corner contributions with plain FMAs into corner-major per-cell sums,
+//          and lets every node of the box gather its (up to) eight cells and add the
+//          total into the float32 gradient grid with one float2 atomic.  When the box
+//          exceeds the shared-memory capacity the tile falls back to the exact box of
+//          its points, of each half, of each 256-point chunk, then to adding each
+//          point's corners directly; so do single points outside their tile's block
+//          (a batch that is not Morton-sorted is correct, only slower).
 #include "bf16_ops.cuh"
 #include "kernels.h"
 #include <algorithm>
+#include <climits>
+#include <cmath>
 
 namespace srn {
 namespace {
@@ -443,14 +448,17 @@ constexpr int CCAP = 512;       // cells of a usable box
 constexpr int NCAP = 1024;      // nodes of a usable box
 
 // Shared memory of k_scat (dynamic): per-point data, the counting sort, per-cell
-// corner sums (corner-major, conflict-free), the tile's points and transforms.
+// corner sums (corner-major, conflict-free) and the carried partial sums.
 struct ScatSmem {
   float cs[16][CCAP];          // corner k, channel e -> cs[k*C + e][cell]
-  float4 wg[ST];               // wx, wy, wz and dL/dy (bf16 x 2 bits) of each point
-  int cnt[CCAP + 1];           // cell counts, then starts
-  unsigned short perm[ST];     // point indices ordered by cell
-  float gs[kMaxGrids * 12];    // this brick's transforms
-  int red[SNT / 32][6];        // block min/max scratch
+  float pl[16][SNT];           // chunk t's last partial sum when its cell goes on past the chunk
+  uint2 tbox[kMaxGrids];       // the tile's node box in every grid (lo and node counts, bytes)
+  float4 wg[ST];               // per point: grid coordinates s (Eq. 2), then, for the points of a
+                               // box pass, the cell weights; .w holds dL/dy (bf16 x 2 bits)
+  int cnt[CCAP + 1];           // cell counts, then starts; all zero between passes
+  alignas(16) unsigned short perm[ST];    // point indices ordered by cell
+  alignas(16) unsigned short pcell[ST];    // the cell of each sorted position
+  int red[2][SNT / 32][6];     // block min/max scratch (alternating between calls)
   int wsum[SNT / 32];          // block scan scratch
 };
 
@@ -461,43 +469,70 @@ struct Box {
 };
 
 // Exact node box of the cells in [mn, mx] (per axis, cell coordinates), reduced over
-// the block; empty when no point was inside the grid.
-__device__ __forceinline__ Box block_box(ScatSmem& s, int (&mn)[3], int (&mx)[3]) {
+// the block; empty when no point was inside the grid.  Consecutive calls alternate
+// between two scratch rows (`parity`), so one barrier per call suffices: a row is
+// rewritten only after every thread has passed the barrier of the call in between.
+__device__ __forceinline__ Box block_box(ScatSmem& s, int (&mn)[3], int (&mx)[3], unsigned& parity) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int (*red)[6] = s.red[parity & 1u];
+  ++parity;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     mn[d] = __reduce_min_sync(0xffffffffu, mn[d]);
     mx[d] = __reduce_max_sync(0xffffffffu, mx[d]);
   }
   if (lane == 0)
-    for (int d = 0; d < 3; ++d) { s.red[warp][d] = mn[d]; s.red[warp][3 + d] = mx[d]; }
+    for (int d = 0; d < 3; ++d) { red[warp][d] = mn[d]; red[warp][3 + d] = mx[d]; }
   __syncthreads();
   Box bx;
   for (int d = 0; d < 3; ++d) {
-    int lo = s.red[0][d], hi = s.red[0][3 + d];
-    for (int q = 1; q < SNT / 32; ++q) { lo = min(lo, s.red[q][d]); hi = max(hi, s.red[q][3 + d]); }
+    int lo = red[0][d], hi = red[0][3 + d];
+    for (int q = 1; q < SNT / 32; ++q) { lo = min(lo, red[q][d]); hi = max(hi, red[q][3 + d]); }
     bx.lo[d] = lo;
     bx.n[d] = hi >= lo ? hi - lo + 2 : 0;
   }
-  __syncthreads();
   bx.ncells = bx.n[0] ? (bx.n[0] - 1) * (bx.n[1] - 1) * (bx.n[2] - 1) : 0;
   bx.ok = bx.ncells > 0 && bx.ncells <= CCAP && bx.n[0] * bx.n[1] * bx.n[2] <= NCAP;
   return bx;
 }
 
-// Counting sort of the points with cid >= 0 by cell, per-cell corner sums, node gather
-// and one atomic per nonzero node of the box.  `mine` marks the points this thread
-// registered (the ones it owns among those whose cid was written).
+// Adds the eight corner weights of one point (wg entry v) times its dL/dy into a.
 template <int C>
-__device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const short (&id)[PPT]) {
+__device__ __forceinline__ void add_corners(float (&a)[8][C], const float4 v) {
+  const float wx = v.x, wy = v.y, wz = v.z, ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
+  const float zy[4] = {az * ay, az * wy, wz * ay, wz * wy};
+  const float2 g = unpack_bf16(__float_as_uint(v.w));
+  const float ge[2] = {g.x, g.y};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float wt = zy[k >> 1] * ((k & 1) ? wx : ax);
+#pragma unroll
+    for (int e = 0; e < C; ++e) a[k][e] = fmaf(wt, ge[e], a[k][e]);
+  }
+}
+
+// Counting sort of the points with id >= 0 by cell (each already holds its rank rk
+// among its cell's points, taken with an atomic on s.cnt), per-cell corner sums, node
+// gather and one atomic per nonzero node of the box.  Leaves s.cnt zero.  The corner sums are balanced over threads: thread t sums the sorted
+// positions 4t..4t+3 run by run.  A run that is a whole cell is stored as the cell's
+// sum; the chunk's last run, when its cell goes on into the next chunk, is parked in
+// pl[.][t]; the chunk's first run, when its cell began in an earlier chunk, is that
+// cell's last piece, and this thread adds the parked pieces of the cell's earlier
+// chunks to it and stores the sum.
+template <int C>
+__device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const short (&id)[PPT],
+                         const int (&rk)[PPT]) {
+  constexpr int NV = 8 * C;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncx = bx.n[0] - 1, ncy = bx.n[1] - 1, ncz = bx.n[2] - 1, ncells = bx.ncells;
-  for (int l = tid; l <= ncells; l += SNT) s.cnt[l] = 0;
-  __syncthreads();
-  int rk[PPT];
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) rk[j] = id[j] >= 0 ? atomicAdd(s.cnt + id[j], 1) : -1;
-  __syncthreads();
+  {  // cells without points must read as zero in the gather
+    const int n4 = (ncells + 3) >> 2;
+    for (int i = tid; i < NV * n4; i += SNT) {
+      const int r = i / n4;
+      reinterpret_cast<float4*>(s.cs[r])[i - r * n4] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  __syncthreads();   // the callers took every point's rank in its cell (s.cnt) before
   {  // block-wide exclusive scan, two consecutive cells per thread
     const int l0 = 2 * tid;
     const int c0 = l0 < ncells ? s.cnt[l0] : 0, c1 = l0 + 1 < ncells ? s.cnt[l0 + 1] : 0;
@@ -520,38 +555,78 @@ __device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const sh
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < PPT; ++j)
-    if (rk[j] >= 0) s.perm[s.cnt[id[j]] + rk[j]] = (unsigned short)(tid + SNT * j);
+    if (rk[j] >= 0) {
+      const int pos = s.cnt[id[j]] + rk[j];
+      s.perm[pos] = (unsigned short)(tid + SNT * j);
+      s.pcell[pos] = (unsigned short)id[j];
+    }
   __syncthreads();
-  for (int l = tid; l < ncells; l += SNT) {
+  const int n_act = s.cnt[ncells];
+  const int q0 = 4 * tid;
+  int head_cell = -1, head_from = 0;   // the chunk's first run, when its cell began in an earlier chunk
+  if (q0 < n_act) {
+    const int nq = min(4, n_act - q0);
+    const uint2 pp = *reinterpret_cast<const uint2*>(s.perm + q0);
+    const uint2 pc = *reinterpret_cast<const uint2*>(s.pcell + q0);
+    const int idx[4] = {(int)(pp.x & 0xffffu), (int)(pp.x >> 16), (int)(pp.y & 0xffffu), (int)(pp.y >> 16)};
+    const int cel[4] = {(int)(pc.x & 0xffffu), (int)(pc.x >> 16), (int)(pc.y & 0xffffu), (int)(pc.y >> 16)};
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = u < nq ? s.wg[idx[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int start0 = s.cnt[cel[0]];
     float a[8][C];
 #pragma unroll
     for (int k = 0; k < 8; ++k)
 #pragma unroll
       for (int e = 0; e < C; ++e) a[k][e] = 0.f;
-    const int s1 = s.cnt[l + 1];
-    for (int q0 = s.cnt[l]; q0 < s1; q0 += 4) {  // four points' loads in flight at a time
-      float4 v[4];
+    int cur = cel[0];
+    bool first = true;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = q0 + u < s1 ? s.wg[s.perm[q0 + u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int u = 0; u < 4; ++u) {
+      if (u < nq) {
+        if (u > 0 && cel[u] != cur) {   // cell cur ended inside the chunk
+          if (first && start0 < q0) head_cell = cur;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float wx = v[u].x, wy = v[u].y, wz = v[u].z, ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
-        const float wt[8] = {az * ay * ax, az * ay * wx, az * wy * ax, az * wy * wx,
-                             wz * ay * ax, wz * ay * wx, wz * wy * ax, wz * wy * wx};
-        const float2 g = unpack_bf16(__float_as_uint(v[u].w));   // zero for the padding slots
-        const float ge[2] = {g.x, g.y};
+          for (int k = 0; k < 8; ++k)
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+            for (int e = 0; e < C; ++e) s.cs[k * C + e][cur] = a[k][e];
 #pragma unroll
-          for (int e = 0; e < C; ++e) a[k][e] = fmaf(wt[k], ge[e], a[k][e]);
+          for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int e = 0; e < C; ++e) a[k][e] = 0.f;
+          cur = cel[u];
+          first = false;
+        }
+        add_corners<C>(a, v[u]);
       }
     }
+    if (s.cnt[cur + 1] > q0 + 4) {   // the last run goes on into the next chunk
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+      for (int k = 0; k < 8; ++k)
 #pragma unroll
-      for (int e = 0; e < C; ++e) s.cs[k * C + e][l] = a[k][e];
+        for (int e = 0; e < C; ++e) s.pl[k * C + e][tid] = a[k][e];
+    } else {
+      if (first && start0 < q0) head_cell = cur;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int e = 0; e < C; ++e) s.cs[k * C + e][cur] = a[k][e];
+    }
+    head_from = start0 >> 2;
   }
   __syncthreads();
+  if (head_cell >= 0) {   // last piece of a cell spanning chunks head_from .. tid
+    float acc[NV];
+#pragma unroll
+    for (int r = 0; r < NV; ++r) acc[r] = s.cs[r][head_cell];
+    for (int j = head_from; j < tid; ++j)
+#pragma unroll
+      for (int r = 0; r < NV; ++r) acc[r] += s.pl[r][j];
+#pragma unroll
+    for (int r = 0; r < NV; ++r) s.cs[r][head_cell] = acc[r];
+  }
+  __syncthreads();
+  for (int l = tid; l <= ncells; l += SNT) s.cnt[l] = 0;   // ready for the next pass
   const int nodes = bx.n[0] * bx.n[1] * bx.n[2];
   const float inv_x = 1.f / (float)bx.n[0], inv_xy = 1.f / (float)(bx.n[0] * bx.n[1]);
   for (int q = tid; q < nodes; q += SNT) {
@@ -582,119 +657,366 @@ __device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const sh
   __syncthreads();
 }
 
+// Cell of a point from its grid coordinates (the clamped s of Eq. 2).
+__device__ __forceinline__ void cell_of(const float4 w, int R, int& cx, int& cy, int& cz) {
+  cx = min((int)w.x, R - 2);
+  cy = min((int)w.y, R - 2);
+  cz = min((int)w.z, R - 2);
+}
+
+// Box pass over this thread's points whose chunk j is in the mask jm (bit j), read from
+// s.wg.  Returns false, having changed nothing, when their box does not fit in shared
+// memory; otherwise replaces their grid coordinates in s.wg by cell weights and runs
+// the pass.
+template <int C>
+__device__ bool masked_pass(ScatSmem& s, unsigned jm, float* dFi, int R, unsigned& parity) {
+  int mn[3] = {1 << 20, 1 << 20, 1 << 20}, mx[3] = {-1, -1, -1};
+#pragma unroll
+  for (int j = 0; j < PPT; ++j)
+    if ((jm >> j) & 1u) {
+      const float4 w = s.wg[threadIdx.x + SNT * j];
+      if (__float_as_uint(w.w) & 0x7fff7fffu) {
+        int cx, cy, cz;
+        cell_of(w, R, cx, cy, cz);
+        mn[0] = min(mn[0], cx); mn[1] = min(mn[1], cy); mn[2] = min(mn[2], cz);
+        mx[0] = max(mx[0], cx); mx[1] = max(mx[1], cy); mx[2] = max(mx[2], cz);
+      }
+    }
+  const Box bx = block_box(s, mn, mx, parity);   // block-uniform
+  if (bx.n[0] == 0) return true;
+  if (!bx.ok) return false;
+  short id[PPT];
+  int rk[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    id[j] = -1;
+    rk[j] = -1;
+    if ((jm >> j) & 1u) {
+      const int p = threadIdx.x + SNT * j;
+      const float4 w = s.wg[p];
+      if (__float_as_uint(w.w) & 0x7fff7fffu) {
+        int cx, cy, cz;
+        cell_of(w, R, cx, cy, cz);
+        id[j] = (short)(((cz - bx.lo[2]) * (bx.n[1] - 1) + (cy - bx.lo[1])) * (bx.n[0] - 1) + (cx - bx.lo[0]));
+        s.wg[p] = make_float4(w.x - (float)cx, w.y - (float)cy, w.z - (float)cz, w.w);
+        rk[j] = atomicAdd(s.cnt + id[j], 1);
+      }
+    }
+  }
+  box_pass<C>(s, bx, dFi, R, id, rk);
+  return true;
+}
+
+// Largest Morton level (a range of 2^L units) whose block keeps the node box of a
+// grid with R nodes per axis, mapped without distortion, within 80% of the capacities.
+int scat_lmax(int R) {
+  const double cells_per_unit = (double)(R - 1) / (double)(1 << kUnitBits);
+  for (int L = 5; L > 0; --L) {
+    const int ext[3] = {1 << ((L + 2) / 3), 1 << ((L + 1) / 3), 1 << (L / 3)};
+    int64_t cells = 1, nodes = 1;
+    for (int d = 0; d < 3; ++d) {
+      const int c = (int)std::ceil(ext[d] * cells_per_unit) + 1;
+      cells *= c;
+      nodes *= c + 1;
+    }
+    if (cells <= CCAP * 4 / 5 && nodes <= NCAP * 4 / 5) return L;
+  }
+  return 0;
+}
+
+// First point of every Morton unit (2 x 2 x 2 bins) that starts a run of that unit in
+// each brick's batch; the other entries keep the -1 they were cleared to.
+__global__ void k_unit_starts(Bricks brp, const float* __restrict__ xyz, int32_t* __restrict__ ustart) {
+  __shared__ Bricks br;
+  load_bricks(brp, br);
+  __syncthreads();
+  const int b = blockIdx.y;
+  const int64_t o = br.off[b], n = br.off[b + 1] - o;
+  int32_t* us = ustart + (int64_t)b * (kUnits + 1);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const float* q = xyz + 3 * (o + p);
+    const uint32_t u = morton_bin(q[0], q[1], q[2]) >> 3;
+    if (p == 0 || (morton_bin(q[-3], q[-2], q[-1]) >> 3) != u) us[u] = (int32_t)p;
+  }
+}
+
+// One CTA per brick.  Units without a recorded start take the next recorded one (a
+// suffix minimum; for a sorted batch this is exact, for any batch the starts become
+// non-decreasing from 0 to n, so the tiles below always partition the brick's points).  Every unit
+// then belongs to the largest aligned range of 2^L units (L <= lmax) holding at most ST
+// points; each such range becomes ceil(points / ST) tiles of consecutive points.
+__global__ void __launch_bounds__(1024) k_tile_list(Bricks brp, TrainWs ws, int lmax) {
+  constexpr int UPT = kUnits / 1024;
+  __shared__ Bricks br;
+  __shared__ int32_t st[kUnits + 1];
+  __shared__ int32_t wred[32];
+  __shared__ int32_t gbase;
+  load_bricks(brp, br);
+  __syncthreads();
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t o = br.off[b];
+  const int32_t n = (int32_t)(br.off[b + 1] - o);
+  const int32_t* us = ws.ustart + (int64_t)b * (kUnits + 1);
+  int32_t loc[UPT];
+  {
+    int32_t m = INT_MAX;
+#pragma unroll
+    for (int k = UPT - 1; k >= 0; --k) {
+      const int32_t v = us[tid * UPT + k];
+      if (v >= 0) m = min(m, v);
+      loc[k] = m;
+    }
+    int32_t incl = loc[0];   // suffix minimum over lanes >= lane
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t y = __shfl_down_sync(0xffffffffu, incl, d);
+      if (lane + d < 32) incl = min(incl, y);
+    }
+    if (lane == 0) wred[warp] = incl;
+    __syncthreads();
+    int32_t after = n;
+    for (int q = warp + 1; q < 32; ++q) after = min(after, wred[q]);
+    const int32_t next = __shfl_down_sync(0xffffffffu, incl, 1);
+    const int32_t excl = lane < 31 ? min(next, after) : after;
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) st[tid * UPT + k] = min(loc[k], excl);
+    // the first point always opens a tile: in a batch that is not sorted, later points
+    // of its unit may have overwritten its recorded start
+    if (tid == 0) { st[0] = 0; st[kUnits] = n; }
+  }
+  __syncthreads();
+  int nt[UPT], lv[UPT];
+  int tot = 0;
+#pragma unroll
+  for (int k = 0; k < UPT; ++k) {
+    const int u = tid * UPT + k;
+    int L = 0;
+    for (int l = lmax; l > 0; --l) {
+      const int a = u & ~((1 << l) - 1);
+      if (st[a + (1 << l)] - st[a] <= ST) { L = l; break; }
+    }
+    lv[k] = L;
+    nt[k] = 0;
+    if ((u & ((1 << L) - 1)) == 0) nt[k] = (st[u + (1 << L)] - st[u] + ST - 1) / ST;
+    tot += nt[k];
+  }
+  int incl = tot;   // block-wide exclusive scan of the tile counts
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) wred[warp] = incl;
+  __syncthreads();
+  int base = incl - tot, all = 0;
+  for (int q = 0; q < 32; ++q) {
+    if (q < warp) base += wred[q];
+    all += wred[q];
+  }
+  if (tid == 0) gbase = atomicAdd(ws.tile_ctr, all);
+  __syncthreads();
+  int idx = gbase + base;
+#pragma unroll
+  for (int k = 0; k < UPT; ++k) {
+    const int u = tid * UPT + k;
+    const int c = nt[k] ? st[u + (1 << lv[k])] - st[u] : 0;
+    for (int t = 0; t < nt[k]; ++t, ++idx) {
+      ScatTile T;
+      T.start = o + st[u] + (int64_t)t * c / nt[k];
+      T.count = (int32_t)((int64_t)(t + 1) * c / nt[k] - (int64_t)t * c / nt[k]);
+      T.code = (uint32_t)b << 20 | (uint32_t)lv[k] << 16 | (uint32_t)u;
+      ws.tiles[idx] = T;
+    }
+  }
+}
+
+// Node box of the tile's block (units [u0, u0 + 2^L)) in grid g, padded by a small
+// margin in s against rounding; returned as bytes lo[3] | n[3] (n = 0: no point of the
+// block is inside the grid).
+__device__ uint2 tile_box(uint32_t code, const float* __restrict__ g, int R) {
+  const int L = (code >> 16) & 15;
+  const uint32_t u0 = code & 0xffffu;
+  const int ext[3] = {1 << ((L + 2) / 3), 1 << ((L + 1) / 3), 1 << (L / 3)};
+  const uint32_t uc[3] = {compact3(u0), compact3(u0 >> 1), compact3(u0 >> 2)};
+  const float unit = 2.f / (float)(1 << kUnitBits);
+  float lo[3], hi[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = -1.f + unit * (float)uc[d];
+    hi[d] = -1.f + unit * (float)(uc[d] + ext[d]);
+  }
+  const float h = 0.5f * (float)(R - 1);
+  uint32_t blo = 0, bn = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float umin = __ldg(g + 4 * d + 3), umax = umin;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float a = __ldg(g + 4 * d + k);
+      const float p = a * lo[k], q = a * hi[k];
+      umin += fminf(p, q);
+      umax += fmaxf(p, q);
+    }
+    if (umax < -1.f || umin > 1.f) return make_uint2(0u, 0u);
+    const float s0 = fminf(fmaxf(fmaf(umin, h, h) - 1e-3f, 0.f), (float)(R - 1));
+    const float s1 = fminf(fmaxf(fmaf(umax, h, h) + 1e-3f, 0.f), (float)(R - 1));
+    const int c0 = min((int)s0, R - 2), c1 = min((int)s1, R - 2);
+    blo |= (uint32_t)c0 << (8 * d);
+    bn |= (uint32_t)(c1 - c0 + 2) << (8 * d);
+  }
+  return make_uint2(blo, bn);
+}
+
 template <int C>
 __global__ void __launch_bounds__(SNT, 3)
-k_scat(Model md, Grads gr, Bricks brp, TileSizes ts, TrainWs ws, const float* __restrict__ xyz) {
+k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
   extern __shared__ __align__(16) unsigned char smraw[];
   ScatSmem& s = *reinterpret_cast<ScatSmem*>(smraw);
-  __shared__ TileMap tm;
   __shared__ Bricks br;
+  __shared__ ScatTile cur_tile;
   load_bricks(brp, br);
   const int tid = threadIdx.x;
   const int M = md.M, R = md.R;
-  if (tid == 0) build_tile_map_sized(br, ts, tm);
-  __syncthreads();
-  const int total = tm.first[br.n];
-  const int per = (total + gridDim.x - 1) / gridDim.x;
-  const int tb = blockIdx.x * per, te = min(total, tb + per);
+  for (int l = tid; l <= CCAP; l += SNT) s.cnt[l] = 0;
+  const int ntiles = ws.tile_ctr[0];
   const int64_t ntot = br.off[br.n];
   const int64_t gsz = (int64_t)R * R * R * C;
-  int cur = -1;
-  for (int tile = tb; tile < te; ++tile) {
-    const int b = brick_of_tile(tm, br.n, tile, cur);
-    if (b != cur) {
-      __syncthreads();
-      cur = b;
-      for (int c = tid; c < M * 12; c += SNT) s.gs[c] = md.G[(int64_t)b * md.sG + c];
+  unsigned parity = 0;
+  for (;;) {
+    // tiles are taken in list order (brick by brick, Morton order inside a brick), so
+    // the CTAs on the GPU at one time work on neighbouring blocks of one brick
+    if (tid == 0) {
+      const int t = atomicAdd(ws.tile_ctr + 1, 1);
+      ScatTile T;
+      T.start = 0; T.count = -1; T.code = 0;
+      if (t < ntiles) T = ws.tiles[t];
+      cur_tile = T;
     }
-    const int tsz = ts.t[b];
-    const int64_t p0 = br.off[b] + (int64_t)(tile - tm.first[b]) * tsz;
-    const int np = (int)min((int64_t)tsz, br.off[b + 1] - p0);
+    __syncthreads();
+    const ScatTile T = cur_tile;
+    if (T.count < 0) break;
+    const int b = (int)(T.code >> 20);
+    const int64_t p0 = T.start;
+    const int np = T.count;
+    const float* Gb = md.G + (int64_t)b * md.sG;
+    for (int i = tid; i < M; i += SNT) s.tbox[i] = tile_box(T.code, Gb + 12 * i, R);
     float px[PPT], py[PPT], pz[PPT];   // this thread's points (tid + 256 j), kept in registers
+    bool mine_in = true;               // every point of this thread lies in the tile's block
+    const int lvl = (int)((T.code >> 16) & 15u);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
       const int p = tid + SNT * j;
       px[j] = py[j] = pz[j] = 0.f;
-      if (p < np) { px[j] = xyz[3 * (p0 + p)]; py[j] = xyz[3 * (p0 + p) + 1]; pz[j] = xyz[3 * (p0 + p) + 2]; }
+      if (p < np) {
+        px[j] = xyz[3 * (p0 + p)]; py[j] = xyz[3 * (p0 + p) + 1]; pz[j] = xyz[3 * (p0 + p) + 2];
+        mine_in &= (((morton_bin(px[j], py[j], pz[j]) >> 3) ^ (T.code & 0xffffu)) >> lvl) == 0u;
+      }
     }
-    __syncthreads();
-    for (int i = 0; i < M; ++i) {
-      const float* gi = s.gs + 12 * i;
-      float* dFi = gr.dF + (int64_t)b * gr.sF + i * gsz;
-      const uint32_t* dY32 = reinterpret_cast<const uint32_t*>(ws.dY) + (int64_t)i * ntot + p0;
-      const __nv_bfloat16* dY16 = ws.dY + (int64_t)i * ntot + p0;
-      // the thread's points: cell, weights and dL/dy, and the cells' bounds
-      Cell cl[PPT];
-      float g0[PPT], g1[PPT];
-      bool on[PPT];
-      int mn[3] = {1 << 20, 1 << 20, 1 << 20}, mx[3] = {-1, -1, -1};
+    const unsigned act = (1u << ((np + SNT - 1) / SNT)) - 1u;   // chunks holding points
+    // dL/dy of grid i is loaded one grid ahead, so its latency hides behind grid i-1
+    uint32_t dyn[PPT];
+    auto load_dy = [&](int i) {
 #pragma unroll
       for (int j = 0; j < PPT; ++j) {
         const int p = tid + SNT * j;
-        on[j] = false;
-        g0[j] = g1[j] = 0.f;
+        dyn[j] = 0u;
+        if (p < np) {
+          if (C == 2) dyn[j] = __ldg(reinterpret_cast<const unsigned int*>(ws.dY) + (int64_t)i * ntot + p0 + p);
+          else dyn[j] = (uint32_t)__bfloat16_as_ushort(ws.dY[(int64_t)i * ntot + p0 + p]);
+        }
+      }
+    };
+    load_dy(0);
+    // s.tbox; the block's boxes bound the points only if all of them lie in the block
+    // (always, for a Morton-sorted batch)
+    const bool in_block = __syncthreads_and(mine_in) != 0;
+    for (int i = 0; i < M; ++i) {
+      uint32_t dcur[PPT];
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) dcur[j] = dyn[j];
+      if (i + 1 < M) load_dy(i + 1);
+      const uint2 tb = s.tbox[i];
+      if (in_block && tb.y == 0u) continue;   // the block lies outside grid i
+      float gi[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) gi[c] = __ldg(Gb + 12 * i + c);
+      float* dFi = gr.dF + (int64_t)b * gr.sF + i * gsz;
+      Box bx;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        bx.lo[d] = (int)((tb.x >> (8 * d)) & 0xffu);
+        bx.n[d] = (int)((tb.y >> (8 * d)) & 0xffu);
+      }
+      bx.ncells = (bx.n[0] - 1) * (bx.n[1] - 1) * (bx.n[2] - 1);
+      bx.ok = in_block && bx.ncells <= CCAP && bx.n[0] * bx.n[1] * bx.n[2] <= NCAP;
+      if (bx.ok) {   // block-uniform
+        short id[PPT];
+        int rk[PPT];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+          const int p = tid + SNT * j;
+          id[j] = -1;
+          rk[j] = -1;
+          if (p < np) {
+            float ux, uy, uz;
+            affine(gi, px[j], py[j], pz[j], ux, uy, uz);
+            const Cell c = make_cell(ux, uy, uz, R);
+            if (c.inside && (dcur[j] & 0x7fff7fffu)) {
+              const int lx = c.cx - bx.lo[0], ly = c.cy - bx.lo[1], lz = c.cz - bx.lo[2];
+              if (lx >= 0 && ly >= 0 && lz >= 0 && lx < bx.n[0] - 1 && ly < bx.n[1] - 1 && lz < bx.n[2] - 1) {
+                id[j] = (short)((lz * (bx.n[1] - 1) + ly) * (bx.n[0] - 1) + lx);
+                s.wg[p] = make_float4(c.wx, c.wy, c.wz, __uint_as_float(dcur[j]));
+                rk[j] = atomicAdd(s.cnt + id[j], 1);
+              } else {   // outside the block's box (rounding at its faces): add the corners directly
+                const float2 g = unpack_bf16(dcur[j]);
+                scatter_point(dFi, c, R, C, g.x, g.y);
+              }
+            }
+          }
+        }
+        box_pass<C>(s, bx, dFi, R, id, rk);
+        continue;
+      }
+      // the block's box is too large, or does not bound the points: exact boxes of the
+      // points, of each half, of each 256-point chunk, else the chunk's points add their
+      // corners directly
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        const int p = tid + SNT * j;
+        if (!((act >> j) & 1u)) continue;
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
         if (p < np) {
           float ux, uy, uz;
           affine(gi, px[j], py[j], pz[j], ux, uy, uz);
-          cl[j] = make_cell(ux, uy, uz, R);
-          if (cl[j].inside) {
-            if (C == 2) {
-              const float2 g = unpack_bf16(dY32[p]);
-              g0[j] = g.x; g1[j] = g.y;
-            } else {
-              g0[j] = __bfloat162float(dY16[p]);
-            }
-            on[j] = g0[j] != 0.f || g1[j] != 0.f;
-          }
-          if (on[j]) {
-            mn[0] = min(mn[0], cl[j].cx); mn[1] = min(mn[1], cl[j].cy); mn[2] = min(mn[2], cl[j].cz);
-            mx[0] = max(mx[0], cl[j].cx); mx[1] = max(mx[1], cl[j].cy); mx[2] = max(mx[2], cl[j].cz);
-          }
+          const Cell c = make_cell(ux, uy, uz, R);
+          w = make_float4((float)c.cx + c.wx, (float)c.cy + c.wy, (float)c.cz + c.wz,
+                          __uint_as_float(c.inside ? dcur[j] : 0u));
         }
+        s.wg[p] = w;
       }
-      Box bx = block_box(s, mn, mx);
-      if (bx.n[0] == 0) continue;   // block-uniform: no contribution to grid i
-      if (bx.ok) {
-        short id[PPT];
+      if (masked_pass<C>(s, act, dFi, R, parity)) continue;
 #pragma unroll
-        for (int j = 0; j < PPT; ++j) {
-          id[j] = -1;
-          if (on[j]) {
-            const int p = tid + SNT * j;
-            id[j] = (short)(((cl[j].cz - bx.lo[2]) * (bx.n[1] - 1) + (cl[j].cy - bx.lo[1])) * (bx.n[0] - 1) +
-                            (cl[j].cx - bx.lo[0]));
-            s.wg[p] = make_float4(cl[j].wx, cl[j].wy, cl[j].wz, __uint_as_float(pack_bf16(g0[j], g1[j])));
+      for (int h = 0; h < PPT / 2; ++h) {
+        const unsigned hm = (3u << (2 * h)) & act;
+        if (!hm) continue;
+        if (hm != act && masked_pass<C>(s, hm, dFi, R, parity)) continue;
+#pragma unroll
+        for (int c = 2 * h; c < 2 * h + 2; ++c) {
+          const unsigned cm = 1u << c;
+          if (!(act & cm)) continue;
+          if (cm != hm && masked_pass<C>(s, cm, dFi, R, parity)) continue;
+          const float4 w = s.wg[tid + SNT * c];
+          if (__float_as_uint(w.w) & 0x7fff7fffu) {
+            Cell cl;
+            cell_of(w, R, cl.cx, cl.cy, cl.cz);
+            cl.wx = w.x - (float)cl.cx; cl.wy = w.y - (float)cl.cy; cl.wz = w.z - (float)cl.cz;
+            const float2 g = unpack_bf16(__float_as_uint(w.w));
+            scatter_point(dFi, cl, R, C, g.x, g.y);
           }
-        }
-        box_pass<C>(s, bx, dFi, R, id);
-        continue;
-      }
-      // the tile's box is too large: a box per 256-point chunk (point j of every thread)
-#pragma unroll
-      for (int c = 0; c < PPT; ++c) {
-        int cmn[3] = {1 << 20, 1 << 20, 1 << 20}, cmx[3] = {-1, -1, -1};
-        if (on[c]) {
-          cmn[0] = cmx[0] = cl[c].cx; cmn[1] = cmx[1] = cl[c].cy; cmn[2] = cmx[2] = cl[c].cz;
-        }
-        const Box cb = block_box(s, cmn, cmx);
-        if (cb.n[0] == 0) continue;
-        if (cb.ok) {
-          short id[PPT];
-#pragma unroll
-          for (int j = 0; j < PPT; ++j) id[j] = -1;
-          if (on[c]) {
-            const int p = tid + SNT * c;
-            id[c] = (short)(((cl[c].cz - cb.lo[2]) * (cb.n[1] - 1) + (cl[c].cy - cb.lo[1])) * (cb.n[0] - 1) +
-                            (cl[c].cx - cb.lo[0]));
-            s.wg[p] = make_float4(cl[c].wx, cl[c].wy, cl[c].wz, __uint_as_float(pack_bf16(g0[c], g1[c])));
-          }
-          box_pass<C>(s, cb, dFi, R, id);
-        } else if (on[c]) {
-          scatter_point(dFi, cl[c], R, C, g0[c], g1[c]);
         }
       }
     }
-    __syncthreads();
   }
 }
 
@@ -706,64 +1028,74 @@ int occupancy(const void* kern, int threads, size_t smem) {
 
 template <int K>
 cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
-                           const TrainWs& ws, const float* xyz, const float* target) {
+                           const TrainWs& ws, const float* xyz, const float* target, const KernelMark* mark) {
+  auto mark_start = [&](int k) { if (mark && mark->which == k) cudaEventRecord(mark->start, L.stream); };
+  auto mark_stop = [&](int k) { if (mark && mark->which == k) cudaEventRecord(mark->stop, L.stream); };
   int tiles = 0;
   for (int b = 0; b < br.n; ++b) tiles += (int)((br.off[b + 1] - br.off[b] + ET - 1) / ET);
   if (tiles == 0) return cudaSuccess;
   cudaError_t e;
+  {  // scatter tiles: aligned Morton blocks of each brick's points
+    int64_t nmax = 0;
+    for (int b = 0; b < br.n; ++b) nmax = std::max<int64_t>(nmax, br.off[b + 1] - br.off[b]);
+    if (nmax > INT32_MAX) return cudaErrorInvalidValue;
+    if ((e = cudaMemsetAsync(ws.ustart, 0xff, sizeof(int32_t) * (kUnits + 1) * br.n, L.stream)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemsetAsync(ws.tile_ctr, 0, 2 * sizeof(int32_t), L.stream)) != cudaSuccess) return e;
+    const int bx = (int)std::min<int64_t>((nmax + 255) / 256, 4 * L.num_sms / std::max(1, br.n) + 1);
+    k_unit_starts<<<dim3(bx, br.n), 256, 0, L.stream>>>(br, xyz, ws.ustart);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_tile_list<<<br.n, 1024, 0, L.stream>>>(br, ws, scat_lmax(md.R));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   {
     const void* kern = dens ? (const void*)k_enc<K, true> : (const void*)k_enc<K, false>;
     const int grid = std::min(tiles, L.num_sms * occupancy(kern, ENT, 0));
+    mark_start(0);
     if (dens) k_enc<K, true><<<grid, ENT, 0, L.stream>>>(md, br, ws, xyz);
     else k_enc<K, false><<<grid, ENT, 0, L.stream>>>(md, br, ws, xyz);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark_stop(0);
   }
   {
     const int smem = MlpLay<K>::BYTES;
     if ((e = cudaFuncSetAttribute(k_mlp<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
       return e;
     const int grid = std::min(tiles, L.num_sms);
+    mark_start(1);
     k_mlp<K><<<grid, NT, smem, L.stream>>>(md, gr, br, ws, target);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark_stop(1);
   }
   {
     const size_t smem = sizeof(ScatSmem);
-    // per-brick tile size: the largest power of two <= ST whose expected cell count in
-    // a grid (tile points x cells per point) stays near 128, so boxes fit in most tiles
-    TileSizes ts{};
-    int stiles = 0;
-    const double cells = (double)(md.R - 1) * (md.R - 1) * (md.R - 1);
-    for (int b = 0; b < br.n; ++b) {
-      const int64_t nb = br.off[b + 1] - br.off[b];
-      int t = ST;
-      while (t > 128 && (double)t * cells > 128.0 * (double)(nb > 0 ? nb : 1)) t >>= 1;
-      ts.t[b] = t;
-      stiles += (int)((nb + t - 1) / t);
-    }
+    mark_start(2);
     if (md.C == 2) {
       if ((e = cudaFuncSetAttribute(k_scat<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-      const int grid = std::min(stiles, L.num_sms * occupancy((const void*)k_scat<2>, SNT, smem));
-      k_scat<2><<<grid, SNT, smem, L.stream>>>(md, gr, br, ts, ws, xyz);
+      const int grid = L.num_sms * occupancy((const void*)k_scat<2>, SNT, smem);
+      k_scat<2><<<grid, SNT, smem, L.stream>>>(md, gr, br, ws, xyz);
     } else {
       if ((e = cudaFuncSetAttribute(k_scat<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-      const int grid = std::min(stiles, L.num_sms * occupancy((const void*)k_scat<1>, SNT, smem));
-      k_scat<1><<<grid, SNT, smem, L.stream>>>(md, gr, br, ts, ws, xyz);
+      const int grid = L.num_sms * occupancy((const void*)k_scat<1>, SNT, smem);
+      k_scat<1><<<grid, SNT, smem, L.stream>>>(md, gr, br, ws, xyz);
     }
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark_stop(2);
+    return cudaSuccess;
   }
 }
 
 }  // namespace
 
 cudaError_t launch_train_bf16(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
-                              const TrainWs& ws, const float* xyz, const float* target) {
+                              const TrainWs& ws, const float* xyz, const float* target, const KernelMark* mark) {
   switch (md.K) {
-    case 16: return launch_train_k<16>(L, dens, md, gr, br, ws, xyz, target);
-    case 32: return launch_train_k<32>(L, dens, md, gr, br, ws, xyz, target);
-    case 64: return launch_train_k<64>(L, dens, md, gr, br, ws, xyz, target);
-    case 128: return launch_train_k<128>(L, dens, md, gr, br, ws, xyz, target);
+    case 16: return launch_train_k<16>(L, dens, md, gr, br, ws, xyz, target, mark);
+    case 32: return launch_train_k<32>(L, dens, md, gr, br, ws, xyz, target, mark);
+    case 64: return launch_train_k<64>(L, dens, md, gr, br, ws, xyz, target, mark);
+    case 128: return launch_train_k<128>(L, dens, md, gr, br, ws, xyz, target, mark);
     default: return cudaErrorInvalidValue;
   }
 }

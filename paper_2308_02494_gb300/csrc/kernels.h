@@ -17,8 +17,15 @@ struct Launch {
 // decoder forward/backward, scatter), batched over bricks.
 cudaError_t launch_forward_bf16(const Launch& L, const Model& md, const Bricks& br, const float* xyz,
                                 float* out);
+// Optional pair of CUDA events recorded around one kernel of the BF16 training pass
+// (which: 0 encoder, 1 decoder, 2 scatter); the measurement hook passes it.
+struct KernelMark {
+  int which;
+  cudaEvent_t start, stop;
+};
 cudaError_t launch_train_bf16(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
-                              const TrainWs& ws, const float* xyz, const float* target);
+                              const TrainWs& ws, const float* xyz, const float* target,
+                              const KernelMark* mark = nullptr);
 // FP32 path: one fused kernel per mode (encoder + SIMT decoder + per-corner scatter).
 cudaError_t launch_query_fp32(const Launch& L, QueryMode mode, const Model& md, const Grads& gr,
                               const Bricks& br, const TrainWs& ws, const float* xyz,

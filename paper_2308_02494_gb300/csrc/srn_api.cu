@@ -81,7 +81,7 @@ void make_layout(const srn_config* c, srn_layout* L) {
 
 // Workspace carving (every piece 256-byte aligned).
 struct WsLayout {
-  size_t state, acc, gsum, rho, herr, sort_tmp, sort_rank, sort_hist, feat, dfeat;
+  size_t state, acc, gsum, rho, herr, sort_tmp, sort_rank, sort_hist, feat, dfeat, ustart, tiles, tile_ctr;
   size_t r_loc, r_rank, r_bid, r_pos, r_xyz, r_val, r_cnt, r_off, total;
 };
 
@@ -100,6 +100,12 @@ WsLayout ws_layout(const srn_config* c, int64_t maxp) {
   const size_t kbytes = c->precision == SRN_BF16 ? sizeof(uint16_t) * c->n_grids * c->channels : 0;
   w.feat = o; o += align256(kbytes * maxp);
   w.dfeat = o; o += align256(kbytes * maxp);
+  // BF16 scatter tiles: unit starts, and at most one tile per unit plus one per 1024 points
+  const bool bf16 = c->precision == SRN_BF16;
+  const int64_t max_tiles = (int64_t)c->n_bricks * (srn::kUnits + 1) + maxp / 1024 + 1;
+  w.ustart = o; o += bf16 ? align256(sizeof(int32_t) * (srn::kUnits + 1) * c->n_bricks) : 0;
+  w.tiles = o; o += bf16 ? align256(sizeof(srn::ScatTile) * max_tiles) : 0;
+  w.tile_ctr = o; o += align256(sizeof(int32_t) * 2);
   w.r_loc = o; o += align256(sizeof(float) * 3 * maxp);
   w.r_rank = o; o += align256(sizeof(uint32_t) * maxp);
   w.r_bid = o; o += align256(sizeof(uint32_t) * maxp);
@@ -146,8 +152,8 @@ struct srn_handle {
   WsLayout wl;
   int num_sms;
   std::vector<GraphEntry> graphs;
-  // measurement hook: a ring of event pairs around the fused query kernel
-  bool timing = false;
+  // measurement hook: a ring of event pairs around the query pass or one of its kernels
+  int32_t timing = SRN_TIME_OFF;
   std::vector<cudaEvent_t> ev_start, ev_stop;
   std::vector<char> ev_used;
   size_t ev_next = 0;
@@ -166,6 +172,9 @@ struct srn_handle {
     w.upstream = 0;
     w.Y = reinterpret_cast<__nv_bfloat16*>(ws + wl.feat);
     w.dY = reinterpret_cast<__nv_bfloat16*>(ws + wl.dfeat);
+    w.ustart = reinterpret_cast<int32_t*>(ws + wl.ustart);
+    w.tiles = reinterpret_cast<srn::ScatTile*>(ws + wl.tiles);
+    w.tile_ctr = reinterpret_cast<int32_t*>(ws + wl.tile_ctr);
     return w;
   }
   srn::Model model() const {
@@ -234,7 +243,11 @@ srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn
   ws.upstream = upstream;
   size_t slot = 0;
   bool timed = false;
-  if (h->timing && !h->ev_start.empty()) {
+  const bool bf16_train = h->cfg.precision == SRN_BF16 && mode != srn::kForward;
+  const bool time_pass = h->timing == SRN_TIME_QUERY;
+  const bool time_kernel = h->timing >= SRN_TIME_ENCODER && bf16_train;
+  srn::KernelMark mark{};
+  if ((time_pass || time_kernel) && !h->ev_start.empty()) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(L.stream, &cap);
     if (cap == cudaStreamCaptureStatusNone) {
@@ -247,7 +260,8 @@ srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn
         h->timed_launches += 1;
         h->ev_used[slot] = 0;
       }
-      cudaEventRecord(h->ev_start[slot], L.stream);
+      if (time_pass) cudaEventRecord(h->ev_start[slot], L.stream);
+      mark = srn::KernelMark{h->timing - SRN_TIME_ENCODER, h->ev_start[slot], h->ev_stop[slot]};
       timed = true;
     }
   }
@@ -257,10 +271,11 @@ srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn
   else if (mode == srn::kForward)
     e = srn::launch_forward_bf16(L, md, br, xyz, out);
   else
-    e = srn::launch_train_bf16(L, mode == srn::kTrainDensity, md, gr, br, ws, xyz, target);
+    e = srn::launch_train_bf16(L, mode == srn::kTrainDensity, md, gr, br, ws, xyz, target,
+                               timed && time_kernel ? &mark : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "query kernel");
   if (timed) {
-    cudaEventRecord(h->ev_stop[slot], L.stream);
+    if (time_pass) cudaEventRecord(h->ev_stop[slot], L.stream);
     h->ev_used[slot] = 1;
   }
   return SRN_OK;
@@ -405,10 +420,12 @@ srn_status srn_destroy(srn_handle* h) {
   return SRN_OK;
 }
 
-srn_status srn_set_timing(srn_handle* h, int32_t enable) {
+srn_status srn_set_timing(srn_handle* h, int32_t target) {
   srn_status s = check_handle(h);
   if (s != SRN_OK) return s;
-  if (enable && h->ev_start.empty()) {
+  if (target < SRN_TIME_OFF || target > SRN_TIME_SCATTER)
+    return fail(SRN_ERR_INVALID_ARG, "srn_set_timing: unknown target %d", (int)target);
+  if (target != SRN_TIME_OFF && h->ev_start.empty()) {
     const int n = 256;
     h->ev_start.resize(n);
     h->ev_stop.resize(n);
@@ -423,7 +440,7 @@ srn_status srn_set_timing(srn_handle* h, int32_t enable) {
   h->ev_next = 0;
   h->timed_ms = 0.0;
   h->timed_launches = 0;
-  h->timing = enable != 0;
+  h->timing = target;
   return SRN_OK;
 }
 

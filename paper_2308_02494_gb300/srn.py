@@ -181,8 +181,12 @@ def srn_render(h, stream, cam: Camera, lut, vmin, vmax, width, height, samples, 
                              _i64(boxes), vox, rgba))
 
 
-def srn_set_timing(h, enable: bool) -> None:
-    _check(load().srn_set_timing(h, 1 if enable else 0))
+SRN_TIME_OFF, SRN_TIME_QUERY, SRN_TIME_ENCODER, SRN_TIME_DECODER, SRN_TIME_SCATTER = range(5)
+
+
+def srn_set_timing(h, target) -> None:
+    """target: SRN_TIME_* (True means SRN_TIME_QUERY, False SRN_TIME_OFF)."""
+    _check(load().srn_set_timing(h, int(target)))
 
 
 def srn_read_timing(h) -> tuple:
