@@ -39,6 +39,24 @@ FLOP_PER_POINT = 2 * (MLP_MACS_FWD + MLP_MACS_BWD)
 KERNELS_PER_STEP = {"bf16": 14, "fp32": 10}
 
 
+# DRAM bytes (read + write) per launch of each training-pass kernel, from the ncu
+# capture summarised in profiles/train_kernels_dd8.txt (the same 8-brick batch and
+# model).  They hold only for the kernel sources they were taken on: any change to those
+# files makes bench report traffic as null until a new capture.
+NCU_TRAFFIC = {"sources_sha1": "d400e87a019ee3c01d4e443ae698db5f53ba7950",
+               "k_scat": 968.9e6, "k_enc": 885.1e6, "k_mlp": 1336.6e6}
+TRAFFIC_SOURCES = ("k_train_bf16.cu", "common.cuh", "bf16_ops.cuh")
+
+
+def measured_traffic(name):
+    import hashlib
+    h = hashlib.sha1()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2308_02494_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return NCU_TRAFFIC.get(name) if h.hexdigest() == NCU_TRAFFIC["sources_sha1"] else None
+
+
 def kernel_rooflines(wl, n_total, kt, hbm, tf_sus, src):
     """Roofline entries of the training-pass kernels from their measured mean times (ms)."""
     m, r, c = wl["grids"], wl["res"], wl["channels"]
@@ -61,7 +79,7 @@ def kernel_rooflines(wl, n_total, kt, hbm, tf_sus, src):
         else:
             ach, peak, unit, psrc = amount / (ms / 1e3) / 1e12, tf_sus, "TFLOP/s", f"{src} bf16 sustained"
         out[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                     "traffic": None, "kernel_ms": ms, "peak_source": psrc, "algorithmic": per,
+                     "traffic": measured_traffic(name) if wl["bricks"] == 8 else None, "kernel_ms": ms, "peak_source": psrc, "algorithmic": per,
                      "algorithmic_per_launch": amount}
     return out
 
