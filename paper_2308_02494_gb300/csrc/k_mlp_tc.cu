@@ -1,0 +1,352 @@
+// Decoder forward and backward of the BF16 training pass for K = M*C = 128 features on
+// the fifth-generation tensor cores (Sec. 4.1.2's MLP 128 -> 64 -> 64 -> 1 without
+// biases, L_rec of Sec. 4.3.1, and its gradient):
+//
+//   Z1 = Y W1^T      H1 = ReLU(Z1)      Z2 = H1 W2^T      H2 = ReLU(Z2)
+//   f  = (H2 . w3)(max - min) + min     dm = dL/df (max - min)
+//   dZ2 = dm w3 [Z2 > 0]   dH1 = dZ2 W2   dZ1 = dH1 [H1 > 0]   dY = dZ1 W1
+//   dW1 += dZ1^T Y   dW2 += dZ2^T H1   dw3 += dm^T H2
+//
+// A CTA of 128 threads takes 128-point tiles.  One thread issues tcgen05.mma with
+// BF16 operands in 128-byte-swizzled shared memory and FP32 accumulators in tensor
+// memory (256 columns per CTA: Z1 / dH1 / dY in columns 0..127, Z2 in 64..127, and
+// the brick's dW1^T and dW2^T accumulated across tiles in 128..255); thread r of the
+// CTA owns tile row r in every epilogue (tcgen05.ld of its tensor-memory lane),
+// applies ReLU / the loss / the masks and writes the next operand back to shared
+// memory as BF16.  The accumulated weight gradients go to global memory with one
+// atomic per entry when the CTA moves to another brick or finishes.  Every wait on
+// the tensor cores is bounded; on giving up the CTA sets bit 1 of the status word,
+// stops, and frees its tensor memory.
+#include "bf16_ops.cuh"
+#include "kernels.h"
+#include "tc_ops.cuh"
+
+namespace srn {
+namespace {
+
+constexpr int TT = 128;    // points per tile (the MMA's M)
+constexpr int TK = 128;    // features (K = M*C)
+constexpr int TNT = 128;   // threads
+constexpr uint32_t kPolls = 1u << 22;
+
+// Shared memory (offsets from a 1024-byte aligned base; operand blocks 1024-aligned).
+struct TcLay {
+  static constexpr uint32_t Y = 0;           // [128 pts][128 feats] bf16
+  static constexpr uint32_t W1 = 32768;      // [64][128]
+  static constexpr uint32_t W2 = 49152;      // [64][64]
+  static constexpr uint32_t H1 = 57344;      // [128][64] ReLU(Z1)
+  static constexpr uint32_t DZ2 = 73728;     // [128][64] dL/dZ2
+  static constexpr uint32_t DZ1 = 90112;     // [128][64] dL/dZ1
+  static constexpr uint32_t W3 = 106496;     // [64] f32
+  static constexpr uint32_t DW3 = W3 + 256;  // [64] f32 reduction scratch
+  static constexpr uint32_t BYTES = DW3 + 256;
+};
+// Tensor-memory columns.
+constexpr uint32_t kColZ1 = 0, kColZ2 = 64, kColDY = 0, kColDW1 = 128, kColDW2 = 192, kCols = 256;
+
+constexpr uint32_t kIdZ = tc::idesc_bf16(128, 64, false, false);    // Z1, Z2
+constexpr uint32_t kIdDH = tc::idesc_bf16(128, 64, false, true);    // dH1 (W2 read transposed)
+constexpr uint32_t kIdDY = tc::idesc_bf16(128, 128, false, true);   // dY (W1 read transposed)
+constexpr uint32_t kIdW = tc::idesc_bf16(128, 64, true, true);      // dW1^T, dW2^T
+
+__device__ __forceinline__ float bits(uint32_t u) { return __uint_as_float(u); }
+
+__global__ void __launch_bounds__(TNT, 2)
+k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ target) {
+  extern __shared__ unsigned char raw[];
+  __shared__ TileMap tm;
+  __shared__ Bricks br;
+  __shared__ uint32_t tslot;
+  __shared__ __align__(8) unsigned long long mbar_s;
+  load_bricks(brp, br);
+  const uint32_t base0 = su32(raw), base = (base0 + 1023u) & ~1023u;
+  unsigned char* sm = raw + (base - base0);
+  const uint32_t sY = base + TcLay::Y, sW1 = base + TcLay::W1, sW2 = base + TcLay::W2;
+  const uint32_t sH1 = base + TcLay::H1, sDZ2 = base + TcLay::DZ2, sDZ1 = base + TcLay::DZ1;
+  float* w3s = reinterpret_cast<float*>(sm + TcLay::W3);
+  float* dw3s = reinterpret_cast<float*>(sm + TcLay::DW3);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t mbar = su32(&mbar_s);
+  if (tid == 0) {
+    build_tile_map(br, TT, tm);
+    tc::mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(su32(&tslot), kCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
+  const int total = tm.first[br.n];
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int tb = blockIdx.x * per, te = min(total, tb + per);
+  const int64_t ntot = br.off[br.n];
+  const int r = tid;   // the tile row this thread owns in the epilogues
+
+  uint32_t phase = 0;
+  bool gave_up = false;
+  auto wait_mma = [&]() {
+    if (tc::mbar_wait(mbar, phase, kPolls)) phase ^= 1u;
+    else gave_up = true;   // the phase stays: the final wait below retries it
+    tc::fence_after_sync();
+  };
+
+  float dw3[64];
+#pragma unroll
+  for (int j = 0; j < 64; ++j) dw3[j] = 0.f;
+  double sum_r2 = 0.0;
+
+  // Weight gradients of brick b: tensor memory (dW1^T, dW2^T) and registers (dw3) to
+  // global memory.  Every MMA of the brick has completed (each tile waits for its last).
+  auto flush = [&](int b) {
+    tc::fence_after_sync();
+    float* gW1 = gr.dW1 + (int64_t)b * gr.sW1;   // [64][128]
+    float* gW2 = gr.dW2 + (int64_t)b * gr.sW2;   // [64][64]
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      uint32_t d[16];
+      tc::ld16(trow + kColDW1 + c0, d);
+      tc::ld_wait();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) atomicAdd(gW1 + (c0 + j) * TK + r, bits(d[j]));
+    }
+    if (warp < 2) {   // dW2^T lives in lanes 0..63
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        uint32_t d[16];
+        tc::ld16(trow + kColDW2 + c0, d);
+        tc::ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) atomicAdd(gW2 + (c0 + j) * 64 + r, bits(d[j]));
+      }
+    }
+    if (tid < 64) dw3s[tid] = 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      float v = dw3[j];
+      v += __shfl_xor_sync(0xffffffffu, v, 16);
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 4);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      if (lane == 0) atomicAdd(dw3s + j, v);
+      dw3[j] = 0.f;
+    }
+    __syncthreads();
+    if (tid < 64) atomicAdd(gr.dw3 + (int64_t)b * gr.sw3 + tid, dw3s[tid]);
+    double s = sum_r2;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) atomicAdd(ws.acc + b * kAccPerBrick + ACC_SUM_R2, s);
+    sum_r2 = 0.0;
+    tc::fence_before_sync();
+    __syncthreads();
+  };
+
+  int cur = -1;
+  bool fresh = true;   // first tile of a brick: the dW accumulators start over
+  float span = 0.f, vmin = 0.f, inv_n = 0.f;
+  for (int tile = tb; tile < te; ++tile) {
+    const int b = brick_of_tile(tm, br.n, tile, cur);
+    if (b != cur) {
+      if (cur >= 0) flush(cur);
+      cur = b;
+      const uint4* w1 = reinterpret_cast<const uint4*>(md.W1h + (int64_t)b * md.sW1);
+      for (int q = tid; q < 64 * TK / 8; q += TNT)
+        *reinterpret_cast<uint4*>(sm + TcLay::W1 + tc::sw128_off(q >> 4, (q & 15) * 8, 64)) = w1[q];
+      const uint4* w2 = reinterpret_cast<const uint4*>(md.W2h + (int64_t)b * md.sW2);
+      for (int q = tid; q < 64 * 64 / 8; q += TNT)
+        *reinterpret_cast<uint4*>(sm + TcLay::W2 + tc::sw128_off(q >> 3, (q & 7) * 8, 64)) = w2[q];
+      if (tid < 64) w3s[tid] = md.w3[(int64_t)b * md.sw3 + tid];
+      vmin = md.range[2 * b];
+      span = md.range[2 * b + 1] - vmin;
+      inv_n = 1.f / (float)(br.off[b + 1] - br.off[b]);
+      fresh = true;
+    }
+    const int64_t p0 = br.off[b] + (int64_t)(tile - tm.first[b]) * TT;
+    const int np = (int)min((int64_t)TT, br.off[b + 1] - p0);
+    // ---- the tile's features (16-byte asynchronous copies; rows past np zero-filled)
+    for (int q = tid; q < TT * TK / 8; q += TNT) {
+      const int row = q >> 4, ch = q & 15;
+      const bool valid = row < np;
+      cp_async16(sY + tc::sw128_off(row, ch * 8, TT), ws.Y + (valid ? (p0 + row) * TK + ch * 8 : 0), valid ? 16 : 0);
+    }
+    const bool rv = r < np;
+    const float vr = rv ? target[p0 + r] : 0.f;
+    cp_async_wait_all();
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+
+    // ---- Z1 = Y W1^T
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < TK / 16; ++kk)
+        tc::mma(tmem + kColZ1, tc::desc_kmajor(sY, kk, TT), tc::desc_kmajor(sW1, kk, 64), kIdZ, kk > 0);
+      tc::commit(mbar);
+    }
+    wait_mma();
+    // ---- H1 = ReLU(Z1) -> shared memory
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      uint32_t z[16], h[8];
+      tc::ld16(trow + kColZ1 + c0, z);
+      tc::ld_wait();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = pack_bf16(fmaxf(bits(z[2 * j]), 0.f), fmaxf(bits(z[2 * j + 1]), 0.f));
+      *reinterpret_cast<uint4*>(sm + TcLay::H1 + tc::sw128_off(r, c0, TT)) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(sm + TcLay::H1 + tc::sw128_off(r, c0 + 8, TT)) = make_uint4(h[4], h[5], h[6], h[7]);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+
+    // ---- Z2 = H1 W2^T
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc::mma(tmem + kColZ2, tc::desc_kmajor(sH1, kk, TT), tc::desc_kmajor(sW2, kk, 64), kIdZ, kk > 0);
+      tc::commit(mbar);
+    }
+    wait_mma();
+    // ---- f, the loss, dm; dZ2 -> shared memory; dw3
+    float m = 0.f;
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      uint32_t z[16];
+      tc::ld16(trow + kColZ2 + c0, z);
+      tc::ld_wait();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) m = fmaf(fmaxf(bits(z[j]), 0.f), w3s[c0 + j], m);
+    }
+    float dm;
+    if (ws.upstream) {   // caller-supplied dL/df: dL/dm = dL/df (max - min)
+      dm = rv ? vr * span : 0.f;
+    } else {             // L_rec: dL/dm = 2 (f - v) (max - min) / N
+      const float e = rv ? fmaf(m, span, vmin) - vr : 0.f;
+      if (rv) ws.herr[p0 + r] = e * e;
+      sum_r2 += (double)e * e;
+      dm = 2.f * e * span * inv_n;
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      uint32_t z[16], d[8];
+      tc::ld16(trow + kColZ2 + c0, z);
+      tc::ld_wait();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) dw3[c0 + j] = fmaf(dm, fmaxf(bits(z[j]), 0.f), dw3[c0 + j]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float a = bits(z[2 * j]) > 0.f ? dm * w3s[c0 + 2 * j] : 0.f;
+        const float c = bits(z[2 * j + 1]) > 0.f ? dm * w3s[c0 + 2 * j + 1] : 0.f;
+        d[j] = pack_bf16(a, c);
+      }
+      *reinterpret_cast<uint4*>(sm + TcLay::DZ2 + tc::sw128_off(r, c0, TT)) = make_uint4(d[0], d[1], d[2], d[3]);
+      *reinterpret_cast<uint4*>(sm + TcLay::DZ2 + tc::sw128_off(r, c0 + 8, TT)) = make_uint4(d[4], d[5], d[6], d[7]);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+
+    // ---- dH1 = dZ2 W2 and dW2^T += H1^T dZ2 (rows 64..127 of that MMA read the dZ2
+    //      block as a second A atom and are discarded)
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc::mma(tmem + kColZ1, tc::desc_kmajor(sDZ2, kk, TT), tc::desc_mnmajor(sW2, kk, 64), kIdDH, kk > 0);
+#pragma unroll
+      for (int kk = 0; kk < TT / 16; ++kk)
+        tc::mma(tmem + kColDW2, tc::sdesc(sH1 + (uint32_t)kk * 2048u, TcLay::DZ2 - TcLay::H1, 1024u),
+                tc::desc_mnmajor(sDZ2, kk, TT), kIdW, !(fresh && kk == 0));
+      tc::commit(mbar);
+    }
+    wait_mma();
+    // ---- dZ1 = dH1 [H1 > 0] -> shared memory
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      uint32_t z[16], d[8];
+      tc::ld16(trow + kColZ1 + c0, z);
+      tc::ld_wait();
+      const uint4 ha = *reinterpret_cast<const uint4*>(sm + TcLay::H1 + tc::sw128_off(r, c0, TT));
+      const uint4 hb = *reinterpret_cast<const uint4*>(sm + TcLay::H1 + tc::sw128_off(r, c0 + 8, TT));
+      const uint32_t hw[8] = {ha.x, ha.y, ha.z, ha.w, hb.x, hb.y, hb.z, hb.w};
+#pragma unroll
+      for (int j = 0; j < 8; ++j)   // ReLU outputs are never negative: > 0 iff nonzero
+        d[j] = pack_bf16((hw[j] & 0x7fffu) ? bits(z[2 * j]) : 0.f, (hw[j] & 0x7fff0000u) ? bits(z[2 * j + 1]) : 0.f);
+      *reinterpret_cast<uint4*>(sm + TcLay::DZ1 + tc::sw128_off(r, c0, TT)) = make_uint4(d[0], d[1], d[2], d[3]);
+      *reinterpret_cast<uint4*>(sm + TcLay::DZ1 + tc::sw128_off(r, c0 + 8, TT)) = make_uint4(d[4], d[5], d[6], d[7]);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+
+    // ---- dY = dZ1 W1 and dW1^T += Y^T dZ1
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        tc::mma(tmem + kColDY, tc::desc_kmajor(sDZ1, kk, TT), tc::desc_mnmajor(sW1, kk, 64), kIdDY, kk > 0);
+#pragma unroll
+      for (int kk = 0; kk < TT / 16; ++kk)
+        tc::mma(tmem + kColDW1, tc::desc_mnmajor(sY, kk, TT), tc::desc_mnmajor(sDZ1, kk, TT), kIdW,
+                !(fresh && kk == 0));
+      tc::commit(mbar);
+    }
+    wait_mma();
+    // ---- dL/dy to global memory, grid-major bf16: dY[i][p][c] (column 2i + c)
+#pragma unroll
+    for (int c0 = 0; c0 < TK; c0 += 16) {
+      uint32_t z[16];
+      tc::ld16(trow + kColDY + c0, z);
+      tc::ld_wait();
+      if (rv && md.C == 2) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          reinterpret_cast<uint32_t*>(ws.dY)[(int64_t)(c0 / 2 + i) * ntot + p0 + r] =
+              pack_bf16(bits(z[2 * i]), bits(z[2 * i + 1]));
+      } else if (rv) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) ws.dY[(int64_t)(c0 + i) * ntot + p0 + r] = __float2bfloat16_rn(bits(z[i]));
+      }
+    }
+    fresh = false;
+    tc::fence_before_sync();
+    if (__syncthreads_or(gave_up)) {
+      gave_up = true;
+      break;
+    }
+  }
+  if (gave_up) {   // let MMAs still in flight finish (bounded) before freeing tensor memory
+    tc::mbar_wait(mbar, phase, kPolls);
+    if (tid == 0) atomicOr(ws.status, 2);
+  } else if (cur >= 0) {
+    flush(cur);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+}
+
+}  // namespace
+
+// The decoder pass of the BF16 training step when K = 128 (2 CTAs per SM).
+cudaError_t launch_mlp_tc(const Launch& L, const Model& md, const Grads& gr, const Bricks& br, const TrainWs& ws,
+                          const float* target) {
+  if (md.K != TK) return cudaErrorInvalidValue;
+  int tiles = 0;
+  for (int b = 0; b < br.n; ++b) tiles += (int)((br.off[b + 1] - br.off[b] + TT - 1) / TT);
+  if (tiles == 0) return cudaSuccess;
+  const int smem = (int)TcLay::BYTES + 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(tiles, 2 * L.num_sms);
+  k_mlp_tc<<<grid, TNT, smem, L.stream>>>(md, gr, br, ws, target);
+  return cudaGetLastError();
+}
+
+}  // namespace srn

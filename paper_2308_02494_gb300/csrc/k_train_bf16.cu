@@ -1057,7 +1057,11 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark_stop(0);
   }
-  {
+  if constexpr (K == 128) {   // tcgen05 decoder
+    mark_start(1);
+    if ((e = launch_mlp_tc(L, md, gr, br, ws, target)) != cudaSuccess) return e;
+    mark_stop(1);
+  } else {
     const int smem = MlpLay<K>::BYTES;
     if ((e = cudaFuncSetAttribute(k_mlp<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
       return e;

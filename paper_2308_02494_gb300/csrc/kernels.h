@@ -26,6 +26,9 @@ struct KernelMark {
 cudaError_t launch_train_bf16(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
                               const TrainWs& ws, const float* xyz, const float* target,
                               const KernelMark* mark = nullptr);
+// The decoder kernel of the BF16 training pass on the tcgen05 tensor cores (K = 128).
+cudaError_t launch_mlp_tc(const Launch& L, const Model& md, const Grads& gr, const Bricks& br, const TrainWs& ws,
+                          const float* target);
 // FP32 path: one fused kernel per mode (encoder + SIMT decoder + per-corner scatter).
 cudaError_t launch_query_fp32(const Launch& L, QueryMode mode, const Model& md, const Grads& gr,
                               const Bricks& br, const TrainWs& ws, const float* xyz,

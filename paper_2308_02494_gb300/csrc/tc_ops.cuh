@@ -1,0 +1,107 @@
+// Fifth-generation tensor-core helpers (sm_100 family): shared-memory matrix
+// descriptors, instruction descriptors, tcgen05.mma / commit / ld, tensor-memory
+// allocation, mbarriers with bounded waits, and the 128-byte-swizzled operand layout.
+//
+// Operand layout used throughout: a row-major bf16 matrix [rows][cols] is stored in
+// column blocks of 64 (128 bytes per row); block j holds columns 64j..64j+63 of every
+// row, rows 128 bytes apart, and the 16-byte chunk c of row r sits at chunk c ^ (r % 8)
+// (the hardware's 128-byte swizzle; every block starts on a 1024-byte boundary).  Read
+// with rows along M (or N) and columns along K, this is the "K-major" layout; read with
+// rows along K and columns along M (or N), the same bytes are the "MN-major" layout.
+#pragma once
+#include <cstdint>
+
+namespace srn {
+namespace tc {
+
+// Byte offset of element (r, c) of a [nrows][*] bf16 matrix in the layout above.
+__host__ __device__ constexpr uint32_t sw128_off(uint32_t r, uint32_t c, uint32_t nrows) {
+  return (c >> 6) * (nrows * 128u) + r * 128u + ((((c & 63u) >> 3) ^ (r & 7u)) << 4) + (c & 7u) * 2u;
+}
+
+// Shared-memory matrix descriptor: start address, leading / stride byte offsets,
+// descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// K-step kk (16 bf16 along K) of a K-major operand stored [nrows][K] at saddr.
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr, int kk, uint32_t nrows) {
+  return sdesc(saddr + (uint32_t)((kk * 16) >> 6) * nrows * 128u + (uint32_t)((kk * 16) & 63) * 2u, 16u, 1024u);
+}
+// K-step kk of an MN-major operand stored [K rows][MN] at saddr (nrows = K rows held).
+__device__ __forceinline__ uint64_t desc_mnmajor(uint32_t saddr, int kk, uint32_t nrows) {
+  return sdesc(saddr + (uint32_t)kk * 16u * 128u, nrows * 128u, 1024u);
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B, F32 accumulation, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A * B^T for one K-step; issued by one thread.
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, bool accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate ? 1u : 0u));
+}
+// Arrive on the mbarrier once every tcgen05 operation issued so far by this thread is done.
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Makes this thread's generic-proxy shared-memory writes visible to the tensor cores.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Tensor-memory allocation (a whole warp executes these).  The address is written to
+// shared memory at `dst`.
+__device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 lanes x 32 bits, 16 consecutive columns: thread t of the warp receives lane
+// (taddr's lane + t), columns col .. col + 15.  Follow with ld_wait before use.
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------------ mbarriers
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the mbarrier to complete, giving up after `limit` polls
+// (each poll itself waits a while in hardware).  Returns false on giving up.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
+}
+
+}  // namespace tc
+}  // namespace srn

@@ -128,12 +128,23 @@ def test_backward_matches_oracle(shape, precision, layout):
 
 
 @pytest.mark.parametrize("layout", ["random", "dense"])
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_backward_uneven_bricks(precision, layout):
+@pytest.mark.parametrize("precision,shape", [("fp32", "m8r16c2"), ("bf16", "m8r16c2"), ("bf16", "m64r32c2")])
+def test_backward_uneven_bricks(precision, shape, layout):
+    _uneven_backward_case(precision, layout, shape, [257, 31, 140], 1024, seed=22)
+
+
+def test_backward_bricks_shared_by_one_cta():
+    """More decoder tiles than resident CTAs: CTAs of the BF16 training pass start in
+    one brick and finish in the next (weight reloads and weight-gradient flushes
+    inside a CTA)."""
+    _uneven_backward_case("bf16", "dense", "m64r32c2", [23000, 300, 17000], 41000, seed=30)
+
+
+def _uneven_backward_case(precision, layout, shape, counts, max_points, seed):
     torch = _torch()
-    counts = [257, 31, 140]
-    m, ref = make_model(SHAPES["m8r16c2"], 3, precision, 1024, seed=22)
+    m, ref = make_model(SHAPES[shape], len(counts), precision, max_points, seed=seed)
     xs = _points_for(ref, counts, 8, RND[precision], layout)
+    counts = [len(x) for x in xs]
     r = np.random.default_rng(9)
     vs = [r.uniform(0, 1, c).astype(np.float32) for c in counts]
     off = m.offsets_of(counts)
@@ -141,7 +152,7 @@ def test_backward_uneven_bricks(precision, layout):
                         torch.as_tensor(np.concatenate(vs), device="cuda"), off, density=True).cpu().numpy()
     grads = m.get("grads")
     tol = TOL[precision]
-    for b in range(3):
+    for b in range(len(counts)):
         o = _oracle_backward(ref[b], xs[b], vs[b], True, RND[precision])
         assert abs(losses[b, 0] - o["L_rec"]) <= tol * o["L_rec"], b
         assert abs(losses[b, 1] - o["L_den"]) <= tol * abs(o["L_den"]) + 1e-12, b
@@ -265,11 +276,12 @@ def test_render_bricks_matches_oracle():
     assert rel_l2(img, want) <= 1e-4, rel_l2(img, want)
 
 
-def test_autograd_function_equals_the_mse_backward():
+@pytest.mark.parametrize("precision,shape", [("fp32", "m8r16c2"), ("bf16", "m64r32c2")])
+def test_autograd_function_equals_the_mse_backward(precision, shape):
     torch = _torch()
     from paper_2308_02494_gb300.model import APMGSRNFunction
     n = 900
-    m, ref = make_model(SHAPES["m8r16c2"], 1, "fp32", 2048, seed=29)
+    m, ref = make_model(SHAPES[shape], 1, precision, 2048, seed=29)
     x = torch.as_tensor(_points_for(ref, [n], 15)[0], device="cuda")
     v = torch.rand(n, device="cuda")
     params = m.params.clone().requires_grad_(True)
@@ -279,4 +291,6 @@ def test_autograd_function_equals_the_mse_backward():
     g_auto = params.grad.clone()
     m.backward(x, v, [0, n])
     g_mse = m.grads.clone()
-    assert torch.linalg.norm(g_auto - g_mse) <= 1e-5 * torch.linalg.norm(g_mse)
+    # BF16: the upstream dL/df comes from the forward kernel's f, whose last bits may
+    # differ from the training pass's, and BF16 operand rounding can amplify that
+    assert torch.linalg.norm(g_auto - g_mse) <= TOL[precision] * torch.linalg.norm(g_mse)
