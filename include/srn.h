@@ -42,7 +42,7 @@ typedef enum {
   SRN_ERR_INVALID_ARG = 1,     /* null pointer, bad size, inconsistent offsets */
   SRN_ERR_UNSUPPORTED = 2,     /* legal shape this build does not implement */
   SRN_ERR_CUDA = 3,            /* a CUDA call or launch failed */
-  SRN_ERR_DEVICE_TIMEOUT = 4,  /* reserved: no kernel of this build waits on another */
+  SRN_ERR_DEVICE_TIMEOUT = 4,  /* a bounded device-side wait gave up (reported by srn_get_status) */
   SRN_ERR_NONFINITE = 5,       /* a loss came out NaN/Inf (reported by srn_get_status) */
   SRN_ERR_STATE = 6            /* call out of order (e.g. step before any backward) */
 } srn_status;
@@ -223,8 +223,10 @@ srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const 
 srn_status srn_set_timing(srn_handle* h, int32_t target);
 srn_status srn_read_timing(srn_handle* h, double* total_ms, int64_t* launches);
 
-/* Synchronise `stream` and report device-side status: SRN_ERR_NONFINITE if a loss
- * computed since the last call was NaN/Inf (the flag is then cleared), else SRN_OK. */
+/* Synchronise `stream` and report device-side status since the last call (then clear
+ * it): SRN_ERR_DEVICE_TIMEOUT if a kernel gave up a bounded wait on the tensor cores
+ * (its outputs are then invalid), else SRN_ERR_NONFINITE if a loss was NaN/Inf, else
+ * SRN_OK. */
 srn_status srn_get_status(srn_handle* h, void* stream);
 
 #ifdef __cplusplus

@@ -46,7 +46,7 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
   __shared__ TileMap tm;
   __shared__ Bricks br;
   __shared__ float4 xs[ET];
-  __shared__ float gs[kMaxGrids * 12];
+  __shared__ __align__(16) float gs[kMaxGrids * 12];
   __shared__ float dets[kMaxGrids];
   __shared__ float rhos[2][ET];
   __shared__ uint32_t ys[ET][K / 2 + 1];   // bf16 pairs; odd row pitch: conflict-free column writes
@@ -96,7 +96,13 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
 #pragma unroll 2
       for (int i = gsub; i < M; i += 2) {
         float ux, uy, uz;
-        affine(gs + 12 * i, pt.x, pt.y, pt.z, ux, uy, uz);
+        {
+          const float4* g4 = reinterpret_cast<const float4*>(gs + 12 * i);
+          const float4 a = g4[0], c = g4[1], d = g4[2];
+          ux = fmaf(a.x, pt.x, fmaf(a.y, pt.y, fmaf(a.z, pt.z, a.w)));
+          uy = fmaf(c.x, pt.x, fmaf(c.y, pt.y, fmaf(c.z, pt.z, c.w)));
+          uz = fmaf(d.x, pt.x, fmaf(d.y, pt.y, fmaf(d.z, pt.z, d.w)));
+        }
         const Cell c = make_cell(ux, uy, uz, R);
         float f0 = 0.f, f1 = 0.f;
         if (valid && c.inside) trilinear_bf16(Fb + i * gsz, c, R, C, f0, f1);
@@ -527,10 +533,9 @@ __device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const sh
   const int ncx = bx.n[0] - 1, ncy = bx.n[1] - 1, ncz = bx.n[2] - 1, ncells = bx.ncells;
   {  // cells without points must read as zero in the gather
     const int n4 = (ncells + 3) >> 2;
-    for (int i = tid; i < NV * n4; i += SNT) {
-      const int r = i / n4;
-      reinterpret_cast<float4*>(s.cs[r])[i - r * n4] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    for (int l = tid; l < n4; l += SNT)
+#pragma unroll
+      for (int r = 0; r < NV; ++r) reinterpret_cast<float4*>(s.cs[r])[l] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();   // the callers took every point's rank in its cell (s.cnt) before
   {  // block-wide exclusive scan, two consecutive cells per thread
@@ -629,19 +634,23 @@ __device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const sh
   for (int l = tid; l <= ncells; l += SNT) s.cnt[l] = 0;   // ready for the next pass
   const int nodes = bx.n[0] * bx.n[1] * bx.n[2];
   const float inv_x = 1.f / (float)bx.n[0], inv_xy = 1.f / (float)(bx.n[0] * bx.n[1]);
+  const int sy = ncx, sz = ncx * ncy;   // cell index strides
   for (int q = tid; q < nodes; q += SNT) {
     const int qz = (int)(((float)q + 0.5f) * inv_xy);
     const int rxy = q - qz * bx.n[0] * bx.n[1];
     const int qy = (int)(((float)rxy + 0.5f) * inv_x);
     const int qx = rxy - qy * bx.n[0];
+    // node (qx, qy, qz) is corner k = (dx, dy, dz) of cell (qx - dx, qy - dy, qz - dz)
+    const int l0 = (qz * ncy + qy) * ncx + qx;
+    const bool x0 = qx < ncx, x1 = qx > 0, y0 = qy < ncy, y1 = qy > 0, z0 = qz < ncz, z1 = qz > 0;
     float v[C];
 #pragma unroll
     for (int e = 0; e < C; ++e) v[e] = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int ex = qx - (k & 1), ey = qy - ((k >> 1) & 1), ez = qz - (k >> 2);
-      if (ex >= 0 && ey >= 0 && ez >= 0 && ex < ncx && ey < ncy && ez < ncz) {
-        const int l = (ez * ncy + ey) * ncx + ex;
+      const bool in = ((k & 1) ? x1 : x0) && ((k & 2) ? y1 : y0) && ((k & 4) ? z1 : z0);
+      if (in) {
+        const int l = l0 - ((k & 1) ? 1 : 0) - ((k & 2) ? sy : 0) - ((k & 4) ? sz : 0);
 #pragma unroll
         for (int e = 0; e < C; ++e) v[e] += s.cs[k * C + e][l];
       }
@@ -939,8 +948,12 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
       const uint2 tb = s.tbox[i];
       if (in_block && tb.y == 0u) continue;   // the block lies outside grid i
       float gi[12];
-#pragma unroll
-      for (int c = 0; c < 12; ++c) gi[c] = __ldg(Gb + 12 * i + c);
+      {
+        const float4* g4 = reinterpret_cast<const float4*>(Gb + 12 * i);
+        const float4 a = __ldg(g4), c = __ldg(g4 + 1), d = __ldg(g4 + 2);
+        gi[0] = a.x; gi[1] = a.y; gi[2] = a.z; gi[3] = a.w; gi[4] = c.x; gi[5] = c.y;
+        gi[6] = c.z; gi[7] = c.w; gi[8] = d.x; gi[9] = d.y; gi[10] = d.z; gi[11] = d.w;
+      }
       float* dFi = gr.dF + (int64_t)b * gr.sF + i * gsz;
       Box bx;
 #pragma unroll

@@ -646,6 +646,7 @@ srn_status srn_get_status(srn_handle* h, void* stream) {
   if (e == cudaSuccess && v) e = cudaMemsetAsync(h->status(), 0, sizeof v, cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (v & 2) return fail(SRN_ERR_DEVICE_TIMEOUT, "a kernel gave up waiting for the tensor cores");
   if (v & 1) return fail(SRN_ERR_NONFINITE, "a loss was NaN or Inf");
   return SRN_OK;
 }
