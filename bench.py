@@ -276,6 +276,34 @@ def time_steps(m, vol, boxes, off, xyz, tgt, steps, warmup, stream, sync_all):
     return ev0.elapsed_time(ev1)
 
 
+def render_rate(m, boxes, vox, width=1024, height=1024, samples=512):
+    """Frames/s of the headless renderer over the 8-brick model: one orthographic and one
+    perspective view, CUDA events around each frame on its stream."""
+    import torch
+    from paper_2308_02494_gb300 import synth
+    lut = torch.as_tensor(synth.random_lut(3), device="cuda")
+    views = synth.random_views(2, 5)
+    cams = [synth.orbit_camera(views[0][0], views[0][1], True), synth.orbit_camera(views[1][0], views[1][1], False)]
+    rgba = torch.empty((height, width, 4), dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        m.render(cams[0], lut, 0.0, 1.0, 64, 64, samples, (2, 2, 2), boxes, vox, stream=s)   # warm-up
+        s.synchronize()
+        times = []
+        for cam in cams:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            m.render(cam, lut, 0.0, 1.0, width, height, samples, (2, 2, 2), boxes, vox, rgba=rgba, stream=s)
+            e1.record(s)
+            s.synchronize()
+            times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    return {"frames_per_s": 1e3 / ms, "ms_per_frame": ms, "queries_per_s": width * height * samples / (ms / 1e3),
+            "width": width, "height": height, "samples": samples,
+            "views": "orthographic + perspective, random angles (seed 5), random 8-knot LUT (seed 3)",
+            "ms_per_view": times}
+
+
 def run_own(args, workload):
     if args.volume:
         workload = dict(workload, volume=args.volume,
@@ -352,6 +380,9 @@ def run_own(args, workload):
     # end to end through the C ABI: pinned host points/targets -> device, backward+step, losses -> host
     e2e = None
     fp32_plain = None
+    render = None
+    if not args.no_extras and wl["bricks"] == 8:
+        render = render_rate(m, boxes, wl["volume"])
     if not args.no_extras:
         m.sample_points(11, 0, off, xyz)
         m.sample_target(vol, boxes, xyz, off, tgt)
@@ -396,6 +427,8 @@ def run_own(args, workload):
     cfg = dict(wl)
     cfg["points_per_step"] = n_total
     cfg["parallelism"] = f"bricks replicated per GPU x{world}" if world > 1 else "1 GPU"
+    if render:
+        cfg["render"] = render
     if fp32_plain:
         cfg["fp32_plain"] = fp32_plain
         cfg["speedup_vs_fp32_plain"] = value / world / fp32_plain["value"]

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(ST) k_density_scalar(Bricks br, TrainWs ws, fl
 constexpr int DT = 128;   // points per tile
 constexpr int DNT = 256;  // threads
 
-__global__ void __launch_bounds__(DNT)
+__global__ void __launch_bounds__(DNT, 4)
 k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, float eps) {
   __shared__ TileMap tm;
   __shared__ float4 sx[DT];
@@ -225,10 +225,23 @@ __global__ void k_finalize(Bricks br, Model md, TrainWs ws, int density, float* 
 }
 
 // ------------------------------------------------------------ Adam
-__global__ void k_advance(StepState* st, int do_b) {
+// Advances the step counters and computes Adam's bias corrections once (double).
+// Advances the step counters and Adam's bias corrections (powers of beta kept as
+// running double products; a count of 1 restarts them, the state starting zeroed).
+__global__ void k_advance(StepState* st, int do_b, float b1, float b2) {
   st->step += 1;
   st->t_a += 1;
-  if (do_b) st->t_b += 1;
+  st->p1a = st->t_a == 1 ? (double)b1 : st->p1a * (double)b1;
+  st->p2a = st->t_a == 1 ? (double)b2 : st->p2a * (double)b2;
+  if (do_b) {
+    st->t_b += 1;
+    st->p1b = st->t_b == 1 ? (double)b1 : st->p1b * (double)b1;
+    st->p2b = st->t_b == 1 ? (double)b2 : st->p2b * (double)b2;
+  }
+  st->bc1a = (float)(1.0 - st->p1a);
+  st->rbc2a = (float)(1.0 / (1.0 - st->p2a));
+  st->bc1b = st->t_b > 0 ? (float)(1.0 - st->p1b) : 1.f;
+  st->rbc2b = st->t_b > 0 ? (float)(1.0 / (1.0 - st->p2b)) : 1.f;
 }
 
 __device__ __forceinline__ float adam1(float& p, float g, float& m, float& v, float lr, float b1,
@@ -241,40 +254,49 @@ __device__ __forceinline__ float adam1(float& p, float g, float& m, float& v, fl
   return p;
 }
 
+__device__ __forceinline__ void adam4(float4& P, const float4 G, float4& Mm, float4& V, float lr, float b1, float b2,
+                                      float eps, float bc1, float rbc2) {
+  adam1(P.x, G.x, Mm.x, V.x, lr, b1, b2, eps, bc1, rbc2);
+  adam1(P.y, G.y, Mm.y, V.y, lr, b1, b2, eps, bc1, rbc2);
+  adam1(P.z, G.z, Mm.z, V.z, lr, b1, b2, eps, bc1, rbc2);
+  adam1(P.w, G.w, Mm.w, V.w, lr, b1, b2, eps, bc1, rbc2);
+}
+
+// Adam over float4 groups, two groups per thread and iteration (independent loads in
+// flight); group A (F, decoder) also refreshes its BF16 shadow.
 __global__ void k_adam(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, uint16_t* __restrict__ shadow, int64_t n_a,
                        int64_t n_total, int do_b, float lr_a, float lr_b, float b1, float b2,
                        float eps, const StepState* st) {
-  const int ta = st->t_a, tbc = st->t_b;
-  const float bc1a = (float)(1.0 - pow((double)b1, ta)), rbc2a = (float)(1.0 / (1.0 - pow((double)b2, ta)));
-  const float bc1b = (float)(1.0 - pow((double)b1, tbc > 0 ? tbc : 1));
-  const float rbc2b = (float)(1.0 / (1.0 - pow((double)b2, tbc > 0 ? tbc : 1)));
+  const float bc1a = st->bc1a, rbc2a = st->rbc2a, bc1b = st->bc1b, rbc2b = st->rbc2b;
   const int64_t end = do_b ? n_total : n_a;
   const int64_t n4 = end / 4;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = 4 * q;
-    float4 P = reinterpret_cast<float4*>(p)[q];
-    const float4 Gd = reinterpret_cast<const float4*>(g)[q];
-    float4 Mm = reinterpret_cast<float4*>(m)[q];
-    float4 V = reinterpret_cast<float4*>(v)[q];
-    const bool a = i < n_a;   // n_a is a multiple of 64, so a float4 never straddles groups
-    const float lr = a ? lr_a : lr_b, bc1 = a ? bc1a : bc1b, rbc2 = a ? rbc2a : rbc2b;
-    adam1(P.x, Gd.x, Mm.x, V.x, lr, b1, b2, eps, bc1, rbc2);
-    adam1(P.y, Gd.y, Mm.y, V.y, lr, b1, b2, eps, bc1, rbc2);
-    adam1(P.z, Gd.z, Mm.z, V.z, lr, b1, b2, eps, bc1, rbc2);
-    adam1(P.w, Gd.w, Mm.w, V.w, lr, b1, b2, eps, bc1, rbc2);
-    reinterpret_cast<float4*>(p)[q] = P;
-    reinterpret_cast<float4*>(m)[q] = Mm;
-    reinterpret_cast<float4*>(v)[q] = V;
-    if (shadow && a) {
-      uint2 s;
-      s.x = pack_bf16(P.x, P.y);
-      s.y = pack_bf16(P.z, P.w);
-      reinterpret_cast<uint2*>(shadow)[q] = s;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float4* P4 = reinterpret_cast<float4*>(p);
+  const float4* G4 = reinterpret_cast<const float4*>(g);
+  float4* M4 = reinterpret_cast<float4*>(m);
+  float4* V4 = reinterpret_cast<float4*>(v);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += 2 * stride) {
+    const int64_t q2 = q + stride;
+    const bool two = q2 < n4;
+    float4 P = P4[q], Mm = M4[q], V = V4[q];
+    const float4 Gd = G4[q];
+    float4 Pb = make_float4(0.f, 0.f, 0.f, 0.f), Mb = Pb, Vb = Pb, Gb = Pb;
+    if (two) { Pb = P4[q2]; Mb = M4[q2]; Vb = V4[q2]; Gb = G4[q2]; }
+    // n_a is a multiple of 64, so a float4 never straddles the groups
+    const bool a = 4 * q < n_a, ab = 4 * q2 < n_a;
+    adam4(P, Gd, Mm, V, a ? lr_a : lr_b, b1, b2, eps, a ? bc1a : bc1b, a ? rbc2a : rbc2b);
+    P4[q] = P; M4[q] = Mm; V4[q] = V;
+    if (shadow && a) reinterpret_cast<uint2*>(shadow)[q] = make_uint2(pack_bf16(P.x, P.y), pack_bf16(P.z, P.w));
+    if (two) {
+      adam4(Pb, Gb, Mb, Vb, ab ? lr_a : lr_b, b1, b2, eps, ab ? bc1a : bc1b, ab ? rbc2a : rbc2b);
+      P4[q2] = Pb; M4[q2] = Mb; V4[q2] = Vb;
+      if (shadow && ab) reinterpret_cast<uint2*>(shadow)[q2] = make_uint2(pack_bf16(Pb.x, Pb.y), pack_bf16(Pb.z, Pb.w));
     }
   }
 }
 
+// BF16 shadow of the first n parameters (n a multiple of 4).
 __global__ void k_shadow(const float* __restrict__ p, uint16_t* __restrict__ shadow, int64_t n) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n / 4; q += (int64_t)gridDim.x * blockDim.x) {
     const float4 P = reinterpret_cast<const float4*>(p)[q];
@@ -387,7 +409,7 @@ cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, c
   if (e != cudaSuccess) return e;
   int tiles = 0;
   for (int b = 0; b < br.n; ++b) tiles += (int)((br.off[b + 1] - br.off[b] + DT - 1) / DT);
-  const int grid = tiles < 2 * L.num_sms ? tiles : 2 * L.num_sms;
+  const int grid = tiles < 4 * L.num_sms ? tiles : 4 * L.num_sms;   // 4 x 8 warps per SM
   k_density_grad<<<grid, DNT, 0, L.stream>>>(md, br, ws, xyz, eps);
   return cudaGetLastError();
 }
@@ -401,7 +423,7 @@ cudaError_t launch_finalize(const Launch& L, const Bricks& br, const Model& md, 
 cudaError_t launch_adam(const Launch& L, float* p, float* g, float* m, float* v, uint16_t* shadow,
                         int64_t n_a, int64_t n_total, bool do_b, float lr_a, float lr_b,
                         float beta1, float beta2, float eps, StepState* st) {
-  k_advance<<<1, 1, 0, L.stream>>>(st, do_b ? 1 : 0);
+  k_advance<<<1, 1, 0, L.stream>>>(st, do_b ? 1 : 0, beta1, beta2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = (do_b ? n_total : n_a) / 4;

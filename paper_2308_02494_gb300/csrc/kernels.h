@@ -44,6 +44,9 @@ cudaError_t launch_finalize(const Launch& L, const Bricks& br, const Model& md, 
 struct StepState {
   unsigned long long step;   // sampler step (advanced once per srn_step)
   int t_a, t_b;              // Adam step counts of group A (F, decoder) and B (G)
+  float bc1a, rbc2a;         // 1 - beta1^t_a and 1 / (1 - beta2^t_a)
+  float bc1b, rbc2b;         // the same for t_b
+  double p1a, p2a, p1b, p2b; // beta1^t_a, beta2^t_a, beta1^t_b, beta2^t_b (running products)
 };
 cudaError_t launch_adam(const Launch& L, float* p, float* g, float* m, float* v, uint16_t* shadow,
                         int64_t n_a, int64_t n_total, bool do_b, float lr_a, float lr_b,
