@@ -168,6 +168,7 @@ k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, f
     }
     __syncthreads();
     const float* gg = sg + 12 * gi;
+#pragma unroll 4
     for (int p = pg; p < np; p += npg) {
       const float4 x = sx[p];
       float ux, uy, uz, ex, ey, ez;

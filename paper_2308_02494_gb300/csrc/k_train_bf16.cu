@@ -621,14 +621,18 @@ __device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const sh
   }
   __syncthreads();
   if (head_cell >= 0) {   // last piece of a cell spanning chunks head_from .. tid
-    float acc[NV];
+    float acc[NV], acc2[NV];   // two chunks per iteration: independent loads in flight
 #pragma unroll
-    for (int r = 0; r < NV; ++r) acc[r] = s.cs[r][head_cell];
-    for (int j = head_from; j < tid; ++j)
+    for (int r = 0; r < NV; ++r) { acc[r] = s.cs[r][head_cell]; acc2[r] = 0.f; }
+    int j = head_from;
+    for (; j + 1 < tid; j += 2)
+#pragma unroll
+      for (int r = 0; r < NV; ++r) { acc[r] += s.pl[r][j]; acc2[r] += s.pl[r][j + 1]; }
+    if (j < tid)
 #pragma unroll
       for (int r = 0; r < NV; ++r) acc[r] += s.pl[r][j];
 #pragma unroll
-    for (int r = 0; r < NV; ++r) s.cs[r][head_cell] = acc[r];
+    for (int r = 0; r < NV; ++r) s.cs[r][head_cell] = acc[r] + acc2[r];
   }
   __syncthreads();
   for (int l = tid; l <= ncells; l += SNT) s.cnt[l] = 0;   // ready for the next pass
