@@ -3,10 +3,11 @@
 //  k_enc   encoder (Eq. 1-3) and the feature density of Eq. 7.  Low register count,
 //          several CTAs per SM to hide the latency of the corner gathers (L1/L2
 //          resident BF16 grids).  Writes the features Y [N][K] (bf16) and rho [N].
-//  k_mlp   decoder forward and backward on the tensor cores (mma.sync m16n8k16,
-//          BF16 operands, FP32 accumulation): L_rec partial sums, h(x) = (f - v)^2,
-//          dW1/dW2/dw3 accumulated in registers per CTA and flushed once, and
-//          dL/dy written grid-major as bf16 (dY [M][N][C]) for the scatter.
+//  k_mlp   decoder forward and backward for K < 128 on the tensor cores (mma.sync
+//          m16n8k16, BF16 operands, FP32 accumulation): L_rec partial sums,
+//          h(x) = (f - v)^2, dW1/dW2/dw3 accumulated in registers per CTA and flushed
+//          once, and dL/dy written grid-major as bf16 (dY [M][N][C]) for the scatter.
+//          K = 128 runs on tcgen05 instead (k_mlp_tc.cu).
 //  k_scat  adjoint of Eq. 2.  A tile is up to 1024 points of one brick lying in one
 //          aligned Morton range of the sampler's bins (a small axis-aligned block of
 //          the brick), listed by k_unit_starts / k_tile_list.  The CTA takes the grids
