@@ -276,6 +276,20 @@ def time_steps(m, vol, boxes, off, xyz, tgt, steps, warmup, stream, sync_all):
     return ev0.elapsed_time(ev1)
 
 
+def reduce_over_ranks(points, ms, world, device):
+    """Whole-job totals for the JSON line: points summed over the ranks, time of the
+    slowest rank (ranks train disjoint bricks; no other data crosses ranks)."""
+    if world == 1:
+        return points, ms
+    import torch
+    import torch.distributed as dist
+    p = torch.tensor([float(points)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return int(round(p.item())), float(t.item())
+
+
 def render_rate(m, boxes, vox, width=1024, height=1024, samples=512):
     """Frames/s of the headless renderer over the 8-brick model: one orthographic and one
     perspective view, CUDA events around each frame on its stream."""
@@ -329,7 +343,8 @@ def run_own(args, workload):
             dist.barrier()
 
     wl = workload
-    m, vol, boxes, off, xyz, tgt, n_total = setup(wl, seed_offset=0)
+    # every rank trains its own bricks: different models and uneven batch sizes per rank
+    m, vol, boxes, off, xyz, tgt, n_total = setup(wl, seed_offset=rank)
     stream = torch.cuda.Stream()
     clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     # warm up (first call eager, second captures the CUDA graph, the rest replay it)
@@ -338,11 +353,8 @@ def run_own(args, workload):
     ms = time_steps(m, vol, boxes, off, xyz, tgt, args.steps, 0, stream, sync_all)
     clk = clocks.stop()
     m.status(stream)
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = n_total * world * args.steps / (ms / 1e3)
+    points_all, ms = reduce_over_ranks(n_total * args.steps, ms, world, "cuda")
+    value = points_all / (ms / 1e3)
     losses = m.losses.cpu().numpy()
 
     # per-kernel times: the library's CUDA-event hook (events on the launching stream)
@@ -403,7 +415,8 @@ def run_own(args, workload):
                 hl.copy_(m.losses, non_blocking=True)
             stream.synchronize()
             el = time.perf_counter() - t0
-        e2e = {"value": n_total * world * e_steps / el, "unit": UNIT,
+        e_points, e_ms = reduce_over_ranks(n_total * e_steps, el * 1e3, world, "cuda")
+        e2e = {"value": e_points / (e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(hx.numel() * 4 + ht.numel() * 4),
                "d2h_bytes_per_step": int(hl.numel() * 8),
                "path": "srn_backward(SRN_DENSITY) + srn_step with host-pinned points/targets, losses read back"}
@@ -425,8 +438,8 @@ def run_own(args, workload):
         rate, sample = oracle_rate(args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     cfg = dict(wl)
-    cfg["points_per_step"] = n_total
-    cfg["parallelism"] = f"bricks replicated per GPU x{world}" if world > 1 else "1 GPU"
+    cfg["points_per_step"] = points_all // args.steps
+    cfg["parallelism"] = f"{world} GPUs, each training its own 8 bricks (no collective)" if world > 1 else "1 GPU"
     if render:
         cfg["render"] = render
     if fp32_plain:
