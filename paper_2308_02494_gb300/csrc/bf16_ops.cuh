@@ -81,6 +81,41 @@ __device__ __forceinline__ void trilinear_bf16(const __nv_bfloat16* Fi, const Ce
   }
 }
 
+// Eq. 2 for grids of RC nodes per axis known at compile time: one 32-bit node index and
+// eight reads at constant offsets from it.  Same arithmetic as trilinear_bf16.
+template <int RC>
+__device__ __forceinline__ void trilinear_bf16_r(const __nv_bfloat16* Fi, const Cell& c, int C, float& o0,
+                                                 float& o1) {
+  const uint32_t b = ((uint32_t)c.cz * RC + (uint32_t)c.cy) * RC + (uint32_t)c.cx;
+  const float ax = 1.f - c.wx, ay = 1.f - c.wy, az = 1.f - c.wz;
+  if (C == 2) {
+    const unsigned int* p = reinterpret_cast<const unsigned int*>(Fi) + b;
+    const float2 v0 = unpack_bf16(__ldg(p)), v1 = unpack_bf16(__ldg(p + 1));
+    const float2 v2 = unpack_bf16(__ldg(p + RC)), v3 = unpack_bf16(__ldg(p + RC + 1));
+    const float2 v4 = unpack_bf16(__ldg(p + RC * RC)), v5 = unpack_bf16(__ldg(p + RC * RC + 1));
+    const float2 v6 = unpack_bf16(__ldg(p + RC * RC + RC)), v7 = unpack_bf16(__ldg(p + RC * RC + RC + 1));
+    o0 = az * (ay * (ax * v0.x + c.wx * v1.x) + c.wy * (ax * v2.x + c.wx * v3.x)) +
+         c.wz * (ay * (ax * v4.x + c.wx * v5.x) + c.wy * (ax * v6.x + c.wx * v7.x));
+    o1 = az * (ay * (ax * v0.y + c.wx * v1.y) + c.wy * (ax * v2.y + c.wx * v3.y)) +
+         c.wz * (ay * (ax * v4.y + c.wx * v5.y) + c.wy * (ax * v6.y + c.wx * v7.y));
+  } else {
+    const unsigned short* p = reinterpret_cast<const unsigned short*>(Fi) + b;
+    auto ld = [&](uint32_t o) { return __uint_as_float(static_cast<uint32_t>(__ldg(p + o)) << 16); };
+    const float v0 = ld(0), v1 = ld(1), v2 = ld(RC), v3 = ld(RC + 1);
+    const float v4 = ld(RC * RC), v5 = ld(RC * RC + 1), v6 = ld(RC * RC + RC), v7 = ld(RC * RC + RC + 1);
+    o0 = az * (ay * (ax * v0 + c.wx * v1) + c.wy * (ax * v2 + c.wx * v3)) +
+         c.wz * (ay * (ax * v4 + c.wx * v5) + c.wy * (ax * v6 + c.wx * v7));
+    o1 = 0.f;
+  }
+}
+
+// Eq. 2, with the common resolution R = 32 on the constant-offset path.
+__device__ __forceinline__ void trilinear_bf16_any(const __nv_bfloat16* Fi, const Cell& c, int R, int C, float& o0,
+                                                   float& o1) {
+  if (R == 32) trilinear_bf16_r<32>(Fi, c, C, o0, o1);
+  else trilinear_bf16(Fi, c, R, C, o0, o1);
+}
+
 // Adjoint of Eq. 2 for one point: add g * weight into each corner of cell c of the
 // float32 gradient grid (8 float2 / float atomics).
 __device__ __forceinline__ void scatter_point(float* dFi, const Cell& c, int R, int C, float g0, float g1) {

@@ -87,7 +87,7 @@ k_fwd_bf16(Model md, Bricks brp, const float* __restrict__ xyz, float* __restric
         affine(gs + 12 * i, pt.x, pt.y, pt.z, ux, uy, uz);
         const Cell c = make_cell(ux, uy, uz, R);
         float f0 = 0.f, f1 = 0.f;
-        if (valid && c.inside) trilinear_bf16(Fb + i * gsz, c, R, C, f0, f1);
+        if (valid && c.inside) trilinear_bf16_any(Fb + i * gsz, c, R, C, f0, f1);
         if (C == 2)
           *reinterpret_cast<uint32_t*>(sm + L::Y + swz<K>(p, 2 * i)) = pack_bf16(f0, f1);
         else

@@ -106,7 +106,7 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
         }
         const Cell c = make_cell(ux, uy, uz, R);
         float f0 = 0.f, f1 = 0.f;
-        if (valid && c.inside) trilinear_bf16(Fb + i * gsz, c, R, C, f0, f1);
+        if (valid && c.inside) trilinear_bf16_any(Fb + i * gsz, c, R, C, f0, f1);
         if (C == 2) ys[p][i] = pack_bf16(f0, f1);
         else reinterpret_cast<__nv_bfloat16*>(ys[p])[i] = __float2bfloat16_rn(f0);
         if (DENS && valid) rho += dets[i] * flat_top(ux, uy, uz, md.p);
