@@ -204,6 +204,17 @@ srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const 
                       float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
                       const int32_t grid[3], const int64_t* boxes, int64_t vox, float* rgba_dev);
 
+/* Full-volume decode (the decompression of Sec. 7): f at every voxel of a volume of
+ * `vox` voxels per axis modelled by the domain decomposition of Sec. 5.  Voxel (i, j, k)
+ * sits at the global position -1 + 2 (i, j, k) / (vox - 1); along each axis it belongs
+ * to brick min(floor(n i / (vox - 1)), n - 1) of the grid[3] = (I, J, K) bricks (the
+ * Sec. 5.3 hash at that position), and is queried in that brick's local [-1, 1]^3
+ * given by boxes[B][6] (lo xyz, hi xyz voxels, as in srn_render).  out_dev receives
+ * [vox][vox][vox] float32, z slowest.  Batches of at most max_points voxels; FP32 or
+ * BF16 as the handle. */
+srn_status srn_decode(srn_handle* h, void* stream, const int32_t grid[3], const int64_t* boxes, int64_t vox,
+                      float* out_dev);
+
 /* Measurement hook (no counterpart in the paper).  `target` picks what is timed:
  * SRN_TIME_OFF nothing; SRN_TIME_QUERY every launch of the query pass (srn_forward,
  * srn_backward, and srn_train_step when it runs eagerly: the fused kernel, or the

@@ -113,6 +113,31 @@ __global__ void k_render_scatter(int64_t total, const float* __restrict__ loc, c
   }
 }
 
+// Decode: brick-local coordinates of a voxel block in scanline order.
+__global__ void k_decode_gen(DecodeChunk c, float* __restrict__ xyz) {
+  const int64_t n = (int64_t)c.nx * c.ny * c.nz;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(idx % c.nx);
+    const int64_t r = idx / c.nx;
+    const int y = (int)(r % c.ny), z = (int)(r / c.ny);
+    const int v[3] = {c.x0 + x, c.y0 + y, c.z0 + z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)   // voxel index = (p + 1)/2 (vox - 1): global -> brick-local [-1, 1]
+      xyz[3 * idx + a] = ((float)v[a] - (float)c.lo[a]) / (float)(c.hi[a] - c.lo[a]) * 2.f - 1.f;
+  }
+}
+
+// Decode: the block's values (scanline order) into the volume [vox][vox][vox].
+__global__ void k_decode_store(DecodeChunk c, const float* __restrict__ val, float* __restrict__ out) {
+  const int64_t n = (int64_t)c.nx * c.ny * c.nz;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(idx % c.nx);
+    const int64_t r = idx / c.nx;
+    const int y = (int)(r % c.ny), z = (int)(r / c.ny);
+    out[((int64_t)(c.z0 + z) * c.vox + (c.y0 + y)) * c.vox + c.x0 + x] = val[idx];
+  }
+}
+
 // One thread per ray: gather the ray's values in sample order and composite.
 __global__ void k_render_composite(RenderParams rp, int pix0, int npix, const uint32_t* __restrict__ pos,
                                    const float* __restrict__ val, const float* __restrict__ lut,
@@ -172,6 +197,26 @@ cudaError_t launch_render_batch(const Launch& L, const RenderParams& rp, const R
              : launch_query_fp32(L, kForward, md, gr, br, tw, w.xyz, nullptr, w.val);
   if (e != cudaSuccess) return e;
   k_render_composite<<<(npix + 127) / 128, 128, 0, L.stream>>>(rp, pix0, npix, w.pos, w.val, lut, rgba);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_chunk(const Launch& L, const DecodeChunk& c, const RenderWs& w, const Model& md,
+                                float* out) {
+  const int64_t n = (int64_t)c.nx * c.ny * c.nz;
+  if (n == 0) return cudaSuccess;
+  k_decode_gen<<<blocks_for(n, 256, L.num_sms), 256, 0, L.stream>>>(c, w.xyz);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  Bricks br{};
+  br.n = c.n_bricks;
+  br.dev = nullptr;
+  for (int b = 0; b <= c.n_bricks; ++b) br.off[b] = b <= c.brick ? 0 : n;
+  Grads gr{};
+  TrainWs tw{};
+  e = md.F16 ? launch_forward_bf16(L, md, br, w.xyz, w.val)
+             : launch_query_fp32(L, kForward, md, gr, br, tw, w.xyz, nullptr, w.val);
+  if (e != cudaSuccess) return e;
+  k_decode_store<<<blocks_for(n, 256, L.num_sms), 256, 0, L.stream>>>(c, w.val, out);
   return cudaGetLastError();
 }
 

@@ -29,4 +29,15 @@ struct RenderWs {
 cudaError_t launch_render_batch(const Launch& L, const RenderParams& rp, const RenderWs& w, int pix0,
                                 int npix, const Model& md, const float* lut, float* rgba);
 
+// One batch of the full-volume decode: the voxels [x0, x0+nx) x [y0, y0+ny) x [z0, z0+nz)
+// (all in brick `brick`, x fastest) queried in that brick's local coordinates.
+struct DecodeChunk {
+  int64_t vox;
+  int32_t brick, n_bricks;
+  int32_t x0, nx, y0, ny, z0, nz;
+  int32_t lo[3], hi[3];   // the brick's voxel box (its local [-1, 1] corners)
+};
+cudaError_t launch_decode_chunk(const Launch& L, const DecodeChunk& c, const RenderWs& w, const Model& md,
+                                float* out);
+
 }  // namespace srn

@@ -591,6 +591,66 @@ srn_status srn_train_step(srn_handle* h, void* stream, uint64_t seed, const floa
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "graph launch");
 }
 
+srn_status srn_decode(srn_handle* h, void* stream, const int32_t grid[3], const int64_t* boxes, int64_t vox,
+                      float* out) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (!grid || !boxes || !out) return fail(SRN_ERR_INVALID_ARG, "NULL argument");
+  if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1 || grid[0] * grid[1] * grid[2] != h->cfg.n_bricks)
+    return fail(SRN_ERR_INVALID_ARG, "brick grid does not match n_bricks");
+  if (vox < 2) return fail(SRN_ERR_INVALID_ARG, "vox < 2");
+  for (int b = 0; b < h->cfg.n_bricks; ++b)
+    for (int a = 0; a < 3; ++a) {
+      const int64_t lo = boxes[6 * b + a], hi = boxes[6 * b + 3 + a];
+      if (lo < 0 || hi >= vox || hi <= lo) return fail(SRN_ERR_INVALID_ARG, "box of brick %d invalid", b);
+    }
+  // voxel i of an axis with I bricks belongs to brick min(floor(I i / (vox - 1)), I - 1):
+  // brick k holds [ceil(k (vox - 1) / I), ceil((k + 1)(vox - 1) / I) - 1] (the last one up to vox - 1)
+  auto first = [&](int k, int I) { return (int64_t)((k * (vox - 1) + I - 1) / I); };
+  unsigned char* ws = h->ws;
+  srn::RenderWs w{};
+  w.xyz = reinterpret_cast<float*>(ws + h->wl.r_xyz);
+  w.val = reinterpret_cast<float*>(ws + h->wl.r_val);
+  const srn::Model md = h->model();
+  const int64_t cap = h->max_points;
+  for (int bz = 0; bz < grid[2]; ++bz)
+    for (int by = 0; by < grid[1]; ++by)
+      for (int bx = 0; bx < grid[0]; ++bx) {
+        const int b = bx + grid[0] * (by + grid[1] * bz);
+        const int bc[3] = {bx, by, bz};
+        int64_t lo[3], n[3];
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = first(bc[a], grid[a]);
+          const int64_t hi = bc[a] == grid[a] - 1 ? vox - 1 : first(bc[a] + 1, grid[a]) - 1;
+          n[a] = hi - lo[a] + 1;
+        }
+        srn::DecodeChunk c{};
+        c.vox = vox;
+        c.brick = b;
+        c.n_bricks = h->cfg.n_bricks;
+        for (int a = 0; a < 3; ++a) {
+          c.lo[a] = (int32_t)boxes[6 * b + a];
+          c.hi[a] = (int32_t)boxes[6 * b + 3 + a];
+        }
+        if (n[0] <= 0 || n[1] <= 0 || n[2] <= 0) continue;
+        // chunks: whole planes if they fit, else whole rows, else parts of a row
+        const int64_t plane = n[0] * n[1];
+        const int64_t dz = plane <= cap ? std::max<int64_t>(1, cap / plane) : 1;
+        const int64_t dy = plane <= cap ? n[1] : std::max<int64_t>(1, cap / n[0]);
+        const int64_t dx = n[0] <= cap ? n[0] : cap;
+        for (int64_t z = 0; z < n[2]; z += dz)
+          for (int64_t y = 0; y < n[1]; y += dy)
+            for (int64_t x = 0; x < n[0]; x += dx) {
+              c.x0 = (int32_t)(lo[0] + x); c.nx = (int32_t)std::min(dx, n[0] - x);
+              c.y0 = (int32_t)(lo[1] + y); c.ny = (int32_t)std::min(dy, n[1] - y);
+              c.z0 = (int32_t)(lo[2] + z); c.nz = (int32_t)std::min(dz, n[2] - z);
+              cudaError_t e = srn::launch_decode_chunk(h->launch(stream), c, w, md, out);
+              if (e != cudaSuccess) return cuda_fail(e, "decode");
+            }
+      }
+  return SRN_OK;
+}
+
 srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const float* lut,
                       float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
                       const int32_t grid[3], const int64_t* boxes, int64_t vox, float* rgba) {

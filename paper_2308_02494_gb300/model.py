@@ -149,6 +149,13 @@ class SRN:
                       samples, grid, np.asarray(boxes).ravel(), vox, rgba.data_ptr())
         return rgba
 
+    def decode(self, grid, boxes, vox, out=None, stream=None):
+        """f at every voxel of a vox^3 volume through the brick decomposition (srn_decode)."""
+        if out is None:
+            out = torch.empty((vox, vox, vox), dtype=torch.float32, device=self.device)
+        _s.srn_decode(self.handle, _stream_ptr(stream), grid, np.asarray(boxes).ravel(), vox, out.data_ptr())
+        return out
+
     def status(self, stream=None) -> None:
         _s.srn_get_status(self.handle, _stream_ptr(stream))
 

@@ -32,7 +32,7 @@ EXPORTS = (
     "srn_param_layout", "srn_workspace_size", "srn_create", "srn_destroy", "srn_last_error",
     "srn_sync_shadow", "srn_sample_points", "srn_sample_target", "srn_forward", "srn_backward",
     "srn_step", "srn_train_step", "srn_render", "srn_set_timing", "srn_read_timing", "srn_get_status",
-    "srn_sample_points_static",
+    "srn_sample_points_static", "srn_decode",
 )
 SRN_STATIC_SAMPLER_MAX_POINTS = 131072
 SRN_STATIC_SAMPLER_MAX_BRICKS = 8
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
         "srn_set_timing": [P, I32],
         "srn_read_timing": [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)],
         "srn_sample_points_static": [P, U64, U64, I32, I64P, P],
+        "srn_decode": [P, P, ct.POINTER(ct.c_int32), I64P, I64, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -198,6 +199,11 @@ def srn_read_timing(h) -> tuple:
 def srn_sample_points_static(stream, seed, step, n_bricks, offsets, xyz) -> None:
     """Batch sampler that allocates nothing (scratch in a static device array)."""
     _check(load().srn_sample_points_static(stream, seed, step, n_bricks, _i64(offsets), xyz))
+
+
+def srn_decode(h, stream, grid, boxes, vox, out) -> None:
+    g = (ct.c_int32 * 3)(*[int(v) for v in grid])
+    _check(load().srn_decode(h, stream, g, _i64(boxes), int(vox), out))
 
 
 def srn_get_status(h, stream) -> None:
