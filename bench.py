@@ -318,6 +318,26 @@ def render_rate(m, boxes, vox, width=1024, height=1024, samples=512):
             "ms_per_view": times}
 
 
+def decode_rate(m, boxes, vox):
+    """Points/s of the full-volume decode (srn_decode) of the 8-brick model over the
+    whole vox^3 lattice, CUDA events around the call on its stream."""
+    import torch
+    out = torch.empty((vox, vox, vox), dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        from paper_2308_02494_gb300 import synth
+        m.decode((2, 2, 2), synth.brick_boxes(64, (2, 2, 2), ghost=2), 64, stream=s)   # warm-up
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        m.decode((2, 2, 2), boxes, vox, out=out, stream=s)
+        e1.record(s)
+        s.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"points_per_s": vox ** 3 / (ms / 1e3), "ms": ms, "volume": vox,
+            "note": "every voxel of the lattice through its brick's model (BF16 forward), output written to HBM"}
+
+
 def run_own(args, workload):
     if args.volume:
         workload = dict(workload, volume=args.volume,
@@ -393,8 +413,10 @@ def run_own(args, workload):
     e2e = None
     fp32_plain = None
     render = None
+    decode = None
     if not args.no_extras and wl["bricks"] == 8:
         render = render_rate(m, boxes, wl["volume"])
+        decode = decode_rate(m, boxes, wl["volume"])
     if not args.no_extras:
         m.sample_points(11, 0, off, xyz)
         m.sample_target(vol, boxes, xyz, off, tgt)
@@ -442,6 +464,8 @@ def run_own(args, workload):
     cfg["parallelism"] = f"{world} GPUs, each training its own 8 bricks (no collective)" if world > 1 else "1 GPU"
     if render:
         cfg["render"] = render
+    if decode:
+        cfg["decode"] = decode
     if fp32_plain:
         cfg["fp32_plain"] = fp32_plain
         cfg["speedup_vs_fp32_plain"] = value / world / fp32_plain["value"]
