@@ -204,6 +204,16 @@ srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const 
                       float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
                       const int32_t grid[3], const int64_t* boxes, int64_t vox, float* rgba_dev);
 
+/* Checkpointing (no counterpart in the paper beyond saving trained models, Sec. 5.2).
+ * The caller owns and saves the parameters, Adam moments and data ranges; these calls
+ * move the rest of the training state (sampler step, Adam step counts and bias
+ * corrections) as an opaque blob of srn_state_bytes() bytes, tagged with the brick
+ * and grid counts.  Both synchronise `stream`.  Loading a blob of another build or
+ * shape is SRN_ERR_INVALID_ARG. */
+srn_status srn_state_bytes(srn_handle* h, size_t* bytes);
+srn_status srn_save_state(srn_handle* h, void* stream, void* dst, size_t bytes);
+srn_status srn_load_state(srn_handle* h, void* stream, const void* src, size_t bytes);
+
 /* Full-volume decode (the decompression of Sec. 7): f at every voxel of a volume of
  * `vox` voxels per axis modelled by the domain decomposition of Sec. 5.  Voxel (i, j, k)
  * sits at the global position -1 + 2 (i, j, k) / (vox - 1); along each axis it belongs

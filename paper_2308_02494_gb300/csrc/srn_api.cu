@@ -591,6 +591,61 @@ srn_status srn_train_step(srn_handle* h, void* stream, uint64_t seed, const floa
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "graph launch");
 }
 
+namespace {
+// Training state as srn_save_state writes it.
+struct StateBlob {
+  uint32_t magic;      // 'SRNS'
+  uint32_t version;
+  int32_t n_bricks, n_grids;
+  srn::StepState st;
+};
+constexpr uint32_t kStateMagic = 0x534e5253u, kStateVersion = 1;
+}  // namespace
+
+srn_status srn_state_bytes(srn_handle* h, size_t* bytes) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (!bytes) return fail(SRN_ERR_INVALID_ARG, "NULL argument");
+  *bytes = sizeof(StateBlob);
+  return SRN_OK;
+}
+
+srn_status srn_save_state(srn_handle* h, void* stream, void* dst, size_t bytes) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (!dst) return fail(SRN_ERR_INVALID_ARG, "NULL destination");
+  if (bytes < sizeof(StateBlob)) return fail(SRN_ERR_INVALID_ARG, "state buffer of %zu bytes < %zu", bytes, sizeof(StateBlob));
+  StateBlob b{};
+  b.magic = kStateMagic;
+  b.version = kStateVersion;
+  b.n_bricks = h->cfg.n_bricks;
+  b.n_grids = h->cfg.n_grids;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&b.st, h->state(), sizeof(srn::StepState), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_fail(e, "state read");
+  std::memcpy(dst, &b, sizeof b);
+  return SRN_OK;
+}
+
+srn_status srn_load_state(srn_handle* h, void* stream, const void* src, size_t bytes) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (!src) return fail(SRN_ERR_INVALID_ARG, "NULL source");
+  if (bytes < sizeof(StateBlob)) return fail(SRN_ERR_INVALID_ARG, "state buffer of %zu bytes < %zu", bytes, sizeof(StateBlob));
+  StateBlob b;
+  std::memcpy(&b, src, sizeof b);
+  if (b.magic != kStateMagic || b.version != kStateVersion) return fail(SRN_ERR_INVALID_ARG, "not a training state of this build");
+  if (b.n_bricks != h->cfg.n_bricks || b.n_grids != h->cfg.n_grids)
+    return fail(SRN_ERR_INVALID_ARG, "training state of %d bricks x %d grids, handle has %d x %d", b.n_bricks,
+                b.n_grids, h->cfg.n_bricks, h->cfg.n_grids);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(h->state(), &b.st, sizeof(srn::StepState), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_fail(e, "state write");
+  return SRN_OK;
+}
+
 srn_status srn_decode(srn_handle* h, void* stream, const int32_t grid[3], const int64_t* boxes, int64_t vox,
                       float* out) {
   srn_status s = check_handle(h);

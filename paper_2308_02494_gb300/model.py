@@ -149,6 +149,29 @@ class SRN:
                       samples, grid, np.asarray(boxes).ravel(), vox, rgba.data_ptr())
         return rgba
 
+    # ------------------------------------------------------------------ checkpoints
+    def save(self, path, stream=None) -> None:
+        """Write a checkpoint: parameters, Adam moments, data ranges and the library's
+        training state (sampler step, Adam counts), enough to resume bit for bit."""
+        torch.cuda.current_stream().synchronize()
+        s = self.shape
+        np.savez(path, params=self.params.cpu().numpy(), adam_m=self.adam_m.cpu().numpy(),
+                 adam_v=self.adam_v.cpu().numpy(), range=self.range.cpu().numpy(),
+                 state=np.frombuffer(_s.srn_save_state(self.handle, _stream_ptr(stream)), dtype=np.uint8),
+                 shape=np.array([s.n_grids, s.res, s.channels, s.hidden, self.n_bricks, int(self.bf16)]))
+
+    def load(self, path, stream=None) -> None:
+        """Resume from a checkpoint written by save() for the same shape and precision."""
+        z = np.load(path)
+        s = self.shape
+        want = np.array([s.n_grids, s.res, s.channels, s.hidden, self.n_bricks, int(self.bf16)])
+        if not np.array_equal(z["shape"], want):
+            raise ValueError(f"checkpoint of shape {z['shape'].tolist()}, model is {want.tolist()}")
+        for name, t in (("params", self.params), ("adam_m", self.adam_m), ("adam_v", self.adam_v), ("range", self.range)):
+            t.copy_(torch.as_tensor(z[name]))
+        _s.srn_load_state(self.handle, _stream_ptr(stream), z["state"].tobytes())
+        _s.srn_sync_shadow(self.handle, _stream_ptr(stream))
+
     def decode(self, grid, boxes, vox, out=None, stream=None):
         """f at every voxel of a vox^3 volume through the brick decomposition (srn_decode)."""
         if out is None:

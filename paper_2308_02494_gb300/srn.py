@@ -32,7 +32,7 @@ EXPORTS = (
     "srn_param_layout", "srn_workspace_size", "srn_create", "srn_destroy", "srn_last_error",
     "srn_sync_shadow", "srn_sample_points", "srn_sample_target", "srn_forward", "srn_backward",
     "srn_step", "srn_train_step", "srn_render", "srn_set_timing", "srn_read_timing", "srn_get_status",
-    "srn_sample_points_static", "srn_decode",
+    "srn_sample_points_static", "srn_decode", "srn_state_bytes", "srn_save_state", "srn_load_state",
 )
 SRN_STATIC_SAMPLER_MAX_POINTS = 131072
 SRN_STATIC_SAMPLER_MAX_BRICKS = 8
@@ -99,6 +99,9 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
         "srn_read_timing": [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)],
         "srn_sample_points_static": [P, U64, U64, I32, I64P, P],
         "srn_decode": [P, P, ct.POINTER(ct.c_int32), I64P, I64, P],
+        "srn_state_bytes": [P, ct.POINTER(ct.c_size_t)],
+        "srn_save_state": [P, P, P, ct.c_size_t],
+        "srn_load_state": [P, P, P, ct.c_size_t],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -204,6 +207,24 @@ def srn_sample_points_static(stream, seed, step, n_bricks, offsets, xyz) -> None
 def srn_decode(h, stream, grid, boxes, vox, out) -> None:
     g = (ct.c_int32 * 3)(*[int(v) for v in grid])
     _check(load().srn_decode(h, stream, g, _i64(boxes), int(vox), out))
+
+
+def srn_state_bytes(h) -> int:
+    n = ct.c_size_t()
+    _check(load().srn_state_bytes(h, ct.byref(n)))
+    return n.value
+
+
+def srn_save_state(h, stream) -> bytes:
+    n = srn_state_bytes(h)
+    buf = (ct.c_ubyte * n)()
+    _check(load().srn_save_state(h, stream, buf, n))
+    return bytes(buf)
+
+
+def srn_load_state(h, stream, blob: bytes) -> None:
+    buf = (ct.c_ubyte * len(blob)).from_buffer_copy(blob)
+    _check(load().srn_load_state(h, stream, buf, len(blob)))
 
 
 def srn_get_status(h, stream) -> None:
