@@ -60,33 +60,57 @@ __device__ __forceinline__ Ray make_ray(const RenderParams& rp, int pix) {
   return r;
 }
 
-__global__ void k_render_gen(RenderParams rp, int pix0, int npix, float* __restrict__ loc,
-                             uint32_t* __restrict__ rank, uint32_t* __restrict__ bid,
-                             uint32_t* __restrict__ cnt) {
+// Samples of a block take their rank in their brick's bucket in three levels: lanes of
+// a warp with the same brick (match), one shared-memory count per warp group, one global
+// reservation per brick per block.  A block's samples stay together in each bucket.
+__global__ void __launch_bounds__(256) k_render_gen(RenderParams rp, int pix0, int npix, float* __restrict__ loc,
+                                                    uint32_t* __restrict__ rank, uint32_t* __restrict__ bid,
+                                                    uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t s_cnt[SRN_MAX_BRICKS], s_base[SRN_MAX_BRICKS];
+  const int nb = rp.grid[0] * rp.grid[1] * rp.grid[2];
   const int64_t total = (int64_t)npix * rp.samples;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int ray = (int)(idx / rp.samples), j = (int)(idx % rp.samples);
-    const Ray r = make_ray(rp, pix0 + ray);
-    if (!r.hit) { bid[idx] = 0xffffffffu; continue; }
-    const float t = r.t0 + ((float)j + 0.5f) * r.dt;
-    const float p[3] = {r.ox + t * r.dx, r.oy + t * r.dy, r.oz + t * r.dz};
-    int cell[3];
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) s_cnt[k] = 0;
+    __syncthreads();
+    const int64_t idx = base + threadIdx.x;
+    uint32_t b = 0xffffffffu;
+    if (idx < total) {
+      const int ray = (int)(idx / rp.samples), j = (int)(idx % rp.samples);
+      const Ray r = make_ray(rp, pix0 + ray);
+      if (r.hit) {
+        const float t = r.t0 + ((float)j + 0.5f) * r.dt;
+        const float p[3] = {r.ox + t * r.dx, r.oy + t * r.dy, r.oz + t * r.dz};
+        int cell[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {   // Sec. 5.3 hash, clamped to the brick grid
-      const int n = rp.grid[a];
-      cell[a] = min(max((int)floorf((float)n * (p[a] + 1.f) * 0.5f), 0), n - 1);
-    }
-    const int b = cell[0] + rp.grid[0] * (cell[1] + rp.grid[1] * cell[2]);
-    const float half = 0.5f * (float)(rp.vox - 1);
+        for (int a = 0; a < 3; ++a) {   // Sec. 5.3 hash, clamped to the brick grid
+          const int n = rp.grid[a];
+          cell[a] = min(max((int)floorf((float)n * (p[a] + 1.f) * 0.5f), 0), n - 1);
+        }
+        b = (uint32_t)(cell[0] + rp.grid[0] * (cell[1] + rp.grid[1] * cell[2]));
+        const float half = 0.5f * (float)(rp.vox - 1);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {   // global -> brick-local [-1, 1]
-      const float s = (p[a] + 1.f) * half;
-      const float lo = (float)rp.lo[b][a], hi = (float)rp.hi[b][a];
-      loc[3 * idx + a] = (s - lo) / (hi - lo) * 2.f - 1.f;
+        for (int a = 0; a < 3; ++a) {   // global -> brick-local [-1, 1]
+          const float sc = (p[a] + 1.f) * half;
+          const float lo = (float)rp.lo[b][a], hi = (float)rp.hi[b][a];
+          loc[3 * idx + a] = (sc - lo) / (hi - lo) * 2.f - 1.f;
+        }
+      }
     }
-    bid[idx] = (uint32_t)b;
-    rank[idx] = atomicAdd(cnt + b, 1u);
+    const unsigned grp = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(grp) - 1;
+    const uint32_t before = __popc(grp & ((1u << lane) - 1u));
+    uint32_t wbase = 0;
+    if (b != 0xffffffffu && lane == leader) wbase = atomicAdd(s_cnt + b, (uint32_t)__popc(grp));
+    wbase = __shfl_sync(0xffffffffu, wbase, leader);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) s_base[k] = s_cnt[k] ? atomicAdd(cnt + k, s_cnt[k]) : 0u;
+    __syncthreads();
+    if (idx < total) {
+      bid[idx] = b;
+      if (b != 0xffffffffu) rank[idx] = s_base[b] + wbase + before;
+    }
+    __syncthreads();
   }
 }
 
