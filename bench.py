@@ -43,9 +43,9 @@ KERNELS_PER_STEP = {"bf16": 14, "fp32": 10}
 # capture summarised in profiles/train_kernels_dd8.txt (the same 8-brick batch and
 # model).  They hold only for the kernel sources they were taken on: any change to those
 # files makes bench report traffic as null until a new capture.
-NCU_TRAFFIC = {"sources_sha1": "d400e87a019ee3c01d4e443ae698db5f53ba7950",
-               "k_scat": 968.9e6, "k_enc": 885.1e6, "k_mlp": 1336.6e6}
-TRAFFIC_SOURCES = ("k_train_bf16.cu", "common.cuh", "bf16_ops.cuh")
+NCU_TRAFFIC = {"sources_sha1": "2f8806a609d718f46d259d49ecb4b5a244e71210",
+               "k_scat": 965.8e6, "k_enc": 911.4e6, "k_mlp": 1338.6e6}
+TRAFFIC_SOURCES = ("k_train_bf16.cu", "k_mlp_tc.cu", "common.cuh", "bf16_ops.cuh", "tc_ops.cuh")
 
 
 def measured_traffic(name):
