@@ -32,7 +32,8 @@ __device__ __forceinline__ Tv warp_sum(Tv v) {
 // c = sum g rho_s (needed by dL/drho = (g - c)/S) and L_den = mean rho* (k-1) log(rho_s+eps).
 // Per-point scalar chain of Eq. 8 in float32 (the terms whose rho* is not negligible
 // have |k log(rho_s + eps)| of order one, where float32 exp/log are accurate to a
-// few ulp); every sum is carried in float64.
+// few ulp); each thread sums its few points in float32, every sum across threads is
+// carried in float64.
 struct PointDensity {
   float rs, k, lr, star, g;
 };
@@ -58,13 +59,13 @@ __global__ void __launch_bounds__(ST) k_density_scalar(Bricks br, TrainWs ws, fl
   const int total = tm.first[br.n];
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int tb = blockIdx.x * per, te = min(total, tb + per);
-  double c_acc = 0.0, l_acc = 0.0;
+  float c_acc = 0.f, l_acc = 0.f;   // this thread's few points in float32; float64 across
   int cur = -1;
   float invS = 0.f, hbar = 0.f, n = 1.f;
   auto flush = [&](int b) {
-    c_acc = warp_sum(c_acc);
-    l_acc = warp_sum(l_acc);
-    if ((tid & 31) == 0) { red[0][tid >> 5] = c_acc; red[1][tid >> 5] = l_acc; }
+    double cd = warp_sum((double)c_acc);
+    double ld = warp_sum((double)l_acc) / (double)n;
+    if ((tid & 31) == 0) { red[0][tid >> 5] = cd; red[1][tid >> 5] = ld; }
     __syncthreads();
     if (tid == 0) {
       double c = 0.0, l = 0.0;
@@ -73,8 +74,8 @@ __global__ void __launch_bounds__(ST) k_density_scalar(Bricks br, TrainWs ws, fl
       atomicAdd(ws.acc + b * kAccPerBrick + ACC_LDEN, l);
     }
     __syncthreads();
-    c_acc = 0.0;
-    l_acc = 0.0;
+    c_acc = 0.f;
+    l_acc = 0.f;
   };
   for (int tile = tb; tile < te; ++tile) {
     const int b = brick_of_tile(tm, br.n, tile, cur);
@@ -89,8 +90,8 @@ __global__ void __launch_bounds__(ST) k_density_scalar(Bricks br, TrainWs ws, fl
     const int64_t p = br.off[b] + (int64_t)(tile - tm.first[b]) * ST + tid;
     if (p < br.off[b + 1]) {
       const PointDensity d = point_density(ws.rho[p], ws.herr[p], invS, hbar, eps, n);
-      c_acc += (double)d.g * (double)d.rs;
-      l_acc += (double)d.star * ((double)d.k - 1.0) * (double)d.lr / (double)n;
+      c_acc = fmaf(d.g, d.rs, c_acc);
+      l_acc = fmaf(d.star * (d.k - 1.f), d.lr, l_acc);
     }
   }
   if (cur >= 0) flush(cur);

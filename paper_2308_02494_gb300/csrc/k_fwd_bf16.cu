@@ -81,10 +81,16 @@ k_fwd_bf16(Model md, Bricks brp, const float* __restrict__ xyz, float* __restric
       const int p = (warp & 3) * 32 + lane, gsub = warp >> 2;
       const float4 pt = reinterpret_cast<const float4*>(xs)[p];
       const bool valid = p < np;
-#pragma unroll 2
+#pragma unroll 4
       for (int i = gsub; i < M; i += 2) {
         float ux, uy, uz;
-        affine(gs + 12 * i, pt.x, pt.y, pt.z, ux, uy, uz);
+        {
+          const float4* g4 = reinterpret_cast<const float4*>(gs + 12 * i);
+          const float4 a = g4[0], c = g4[1], d = g4[2];
+          ux = fmaf(a.x, pt.x, fmaf(a.y, pt.y, fmaf(a.z, pt.z, a.w)));
+          uy = fmaf(c.x, pt.x, fmaf(c.y, pt.y, fmaf(c.z, pt.z, c.w)));
+          uz = fmaf(d.x, pt.x, fmaf(d.y, pt.y, fmaf(d.z, pt.z, d.w)));
+        }
         const Cell c = make_cell(ux, uy, uz, R);
         float f0 = 0.f, f1 = 0.f;
         if (valid && c.inside) trilinear_bf16_any(Fb + i * gsz, c, R, C, f0, f1);

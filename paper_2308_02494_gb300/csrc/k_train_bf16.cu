@@ -94,7 +94,7 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
       const float4 pt = xs[p];
       const bool valid = p < np;
       float rho = 0.f;
-#pragma unroll 2
+#pragma unroll 4
       for (int i = gsub; i < M; i += 2) {
         float ux, uy, uz;
         {
