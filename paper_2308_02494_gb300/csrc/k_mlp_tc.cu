@@ -145,11 +145,35 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     __syncthreads();
   };
 
+  // The features of tile t+1 are requested as soon as the last MMA of tile t has read
+  // Y, so the copy overlaps tile t's dL/dy epilogue; its targets likewise.
+  int hint = -1;
+  int64_t nxt_p0 = 0;
+  int nxt_np = 0, nxt_b = 0;
+  float nxt_v = 0.f;
+  auto prefetch = [&](int tile) {
+    nxt_b = brick_of_tile(tm, br.n, tile, hint);
+    hint = nxt_b;
+    nxt_p0 = br.off[nxt_b] + (int64_t)(tile - tm.first[nxt_b]) * TT;
+    nxt_np = (int)min((int64_t)TT, br.off[nxt_b + 1] - nxt_p0);
+    for (int q = tid; q < TT * TK / 8; q += TNT) {
+      const int row = q >> 4, ch = q & 15;
+      const bool valid = row < nxt_np;
+      cp_async16(sY + tc::sw128_off(row, ch * 8, TT), ws.Y + (valid ? (nxt_p0 + row) * TK + ch * 8 : 0),
+                 valid ? 16 : 0);
+    }
+    nxt_v = r < nxt_np ? target[nxt_p0 + r] : 0.f;
+  };
+  if (tb < te) prefetch(tb);
+
   int cur = -1;
   bool fresh = true;   // first tile of a brick: the dW accumulators start over
   float span = 0.f, vmin = 0.f, inv_n = 0.f;
   for (int tile = tb; tile < te; ++tile) {
-    const int b = brick_of_tile(tm, br.n, tile, cur);
+    const int b = nxt_b;
+    const int64_t p0 = nxt_p0;
+    const int np = nxt_np;
+    const float vr = nxt_v;
     if (b != cur) {
       if (cur >= 0) flush(cur);
       cur = b;
@@ -165,16 +189,8 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
       inv_n = 1.f / (float)(br.off[b + 1] - br.off[b]);
       fresh = true;
     }
-    const int64_t p0 = br.off[b] + (int64_t)(tile - tm.first[b]) * TT;
-    const int np = (int)min((int64_t)TT, br.off[b + 1] - p0);
-    // ---- the tile's features (16-byte asynchronous copies; rows past np zero-filled)
-    for (int q = tid; q < TT * TK / 8; q += TNT) {
-      const int row = q >> 4, ch = q & 15;
-      const bool valid = row < np;
-      cp_async16(sY + tc::sw128_off(row, ch * 8, TT), ws.Y + (valid ? (p0 + row) * TK + ch * 8 : 0), valid ? 16 : 0);
-    }
+    // ---- the tile's features (requested one tile ahead; rows past np zero-filled)
     const bool rv = r < np;
-    const float vr = rv ? target[p0 + r] : 0.f;
     cp_async_wait_all();
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -298,6 +314,7 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
       tc::commit(mbar);
     }
     wait_mma();
+    if (tile + 1 < te && !gave_up) prefetch(tile + 1);   // Y has been read by every MMA of this tile
     // ---- dL/dy to global memory, grid-major bf16: dY[i][p][c] (column 2i + c)
 #pragma unroll
     for (int c0 = 0; c0 < TK; c0 += 16) {
@@ -327,6 +344,7 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
   } else if (cur >= 0) {
     flush(cur);
   }
+  cp_async_wait_all();   // a feature copy requested ahead may still be in flight
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, kCols);
