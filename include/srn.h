@@ -53,6 +53,9 @@ typedef enum { SRN_FP32 = 0, SRN_BF16 = 1 } srn_precision;
 #define SRN_DENSITY 1u   /* step (2) of Sec. 4.3.2: L_den (Eq. 9) and its gradient into G */
 #define SRN_UPSTREAM 2u  /* srn_backward only: target_dev holds dL/df per point (any upstream
                             loss) instead of v(x); no L_rec is formed; excludes SRN_DENSITY */
+#define SRN_SCHEDULE 4u  /* srn_train_step only: the training routine set by srn_set_schedule
+                            decides, per brick on the device, whether G is trained and the
+                            learning-rate scale; SRN_DENSITY is then ignored */
 
 /* Model and optimiser configuration (Sec. 4.1, 4.2, 6).  Supported in this build:
  * hidden = 64; channels in {1, 2}; K = n_grids*channels in {16, 32, 64, 128};
@@ -193,6 +196,44 @@ srn_status srn_train_step(srn_handle* h, void* stream, uint64_t seed, const floa
                           const int64_t dims[3], const int64_t* boxes, const int64_t* offsets,
                           uint32_t flags, float* xyz_dev, float* target_dev, double* losses_dev);
 
+/* The training routine of Sec. 4.3.2 and the plateau scheduler of Sec. 5.2, applied
+ * per brick on the device by srn_train_step with SRN_SCHEDULE (no host round trip):
+ *   - G (the transforms) is trained from iteration delay_iters + 1 (500 in the paper) ...
+ *   - ... until the mean of L_den over the last density_window density iterations
+ *     (1000) has not dropped by a relative density_rel (1e-4) below the mean of the
+ *     window before, or past density_frac (0.8) of total_iters: then G stays fixed;
+ *   - when L_rec has not dropped by a relative plateau_rel (1e-4) below its best for
+ *     more than plateau_window (500) iterations, the brick's learning rates are
+ *     multiplied by plateau_factor (0.1); at the plateau_max-th (3rd) time the brick
+ *     has finished and its parameters are no longer updated.
+ * srn_set_schedule stores the routine and restarts every brick's state (iteration 0);
+ * density_window <= 4096, all counts positive, 0 < rel, 0 < frac <= 1,
+ * 0 < plateau_factor <= 1.  srn_read_schedule copies the per-brick state to host
+ * memory (synchronising `stream`). */
+typedef struct {
+  int32_t delay_iters;
+  int32_t density_window;
+  float density_rel;
+  float density_frac;
+  int64_t total_iters;
+  int32_t plateau_window;
+  float plateau_rel;
+  float plateau_factor;
+  int32_t plateau_max;
+} srn_schedule;
+typedef struct {
+  int64_t iteration;        /* iterations trained */
+  float lr_scale;           /* plateau_factor ^ plateaus */
+  int32_t plateaus;         /* plateau reductions so far */
+  int32_t finished;         /* 1: the brick is no longer updated */
+  int32_t density_on;       /* 1: G is trained at the next iteration */
+  int32_t density_stopped;  /* 1: early stop or the iteration cutoff has fired */
+  int32_t density_iters;    /* iterations that trained G */
+  double best_rec;          /* lowest L_rec of the plateau test */
+} srn_brick_schedule;
+srn_status srn_set_schedule(srn_handle* h, const srn_schedule* sched);
+srn_status srn_read_schedule(srn_handle* h, void* stream, srn_brick_schedule* out_host);
+
 /* Headless volume render (Sec. 6) of the domain decomposition (Sec. 5.3) into
  * rgba_dev [height][width][4].  Each ray is clipped to [-1,1]^3 and sampled at
  * `samples` midpoints; every sample is hashed to its brick (grid[3] = I, J, K,
@@ -207,8 +248,8 @@ srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const 
 /* Checkpointing (no counterpart in the paper beyond saving trained models, Sec. 5.2).
  * The caller owns and saves the parameters, Adam moments and data ranges; these calls
  * move the rest of the training state (sampler step, Adam step counts and bias
- * corrections) as an opaque blob of srn_state_bytes() bytes, tagged with the brick
- * and grid counts.  Both synchronise `stream`.  Loading a blob of another build or
+ * corrections, and the per-brick training-routine state with its parameters) as an
+ * opaque blob of srn_state_bytes() bytes, tagged with the brick and grid counts.  Both synchronise `stream`.  Loading a blob of another build or
  * shape is SRN_ERR_INVALID_ARG. */
 srn_status srn_state_bytes(srn_handle* h, size_t* bytes);
 srn_status srn_save_state(srn_handle* h, void* stream, void* dst, size_t bytes);

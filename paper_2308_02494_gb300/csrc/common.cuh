@@ -68,6 +68,7 @@ struct TrainWs {
   int32_t* ustart;    // [B][kUnits + 1] first point of each Morton unit (BF16 scatter tiles)
   struct ScatTile* tiles;  // scatter tiles (BF16 training pass)
   int32_t* tile_ctr;  // [0] tiles written, [1] next tile to take
+  const struct BrickSched* sched;   // per-brick training routine, or NULL (caller's flags)
 };
 
 // A scatter tile: `count` (<= 1024) consecutive points of one brick, all in the aligned

@@ -4,6 +4,8 @@
 //   * Adam (Sec. 6) over the flat parameter buffer, plus the BF16 shadow refresh;
 //   * the batch sampler (Philox4x32-10, then a counting sort by 32^3 Morton bin);
 //   * the ground-truth lookup v(x) of Sec. 4.3.1 (trilinear in a float32 volume).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(ST) k_density_scalar(Bricks br, TrainWs ws, fl
       hbar = (float)(ws.acc[b * kAccPerBrick + ACC_SUM_R2] / nb);
     }
     const int64_t p = br.off[b] + (int64_t)(tile - tm.first[b]) * ST + tid;
-    if (p < br.off[b + 1]) {
+    if (p < br.off[b + 1] && !(ws.sched && !ws.sched[b].den_on)) {
       const PointDensity d = point_density(ws.rho[p], ws.herr[p], invS, hbar, eps, n);
       c_acc = fmaf(d.g, d.rs, c_acc);
       l_acc = fmaf(d.star * (d.k - 1.f), d.lr, l_acc);
@@ -154,7 +156,7 @@ k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, f
       __syncthreads();
     }
     const int64_t p0 = br.off[b] + (int64_t)(tile - tm.first[b]) * DT;
-    const int np = (int)min((int64_t)DT, br.off[b + 1] - p0);
+    const int np = (ws.sched && !ws.sched[b].den_on) ? 0 : (int)min((int64_t)DT, br.off[b + 1] - p0);
     if (tid < DT) {
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       float q = 0.f;
@@ -196,6 +198,7 @@ __global__ void k_finalize(Bricks br, Model md, TrainWs ws, int density, float* 
   const int b = blockIdx.x, i = threadIdx.x;
   const double n = (double)(br.off[b + 1] - br.off[b]);
   const double* acc = ws.acc + b * kAccPerBrick;
+  if (ws.sched) density = density && ws.sched[b].den_on;
   if (density && i < md.M) {
     const float* g = md.G + (int64_t)b * md.sG + 12 * i;
     const double a00 = g[0], a01 = g[1], a02 = g[2], a10 = g[4], a11 = g[5], a12 = g[6];
@@ -264,38 +267,107 @@ __device__ __forceinline__ void adam4(float4& P, const float4 G, float4& Mm, flo
   adam1(P.w, G.w, Mm.w, V.w, lr, b1, b2, eps, bc1, rbc2);
 }
 
-// Adam over float4 groups, two groups per thread and iteration (independent loads in
-// flight); group A (F, decoder) also refreshes its BF16 shadow.
-__global__ void k_adam(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, uint16_t* __restrict__ shadow, int64_t n_a,
-                       int64_t n_total, int do_b, float lr_a, float lr_b, float b1, float b2,
-                       float eps, const StepState* st) {
-  const float bc1a = st->bc1a, rbc2a = st->rbc2a, bc1b = st->bc1b, rbc2b = st->rbc2b;
-  const int64_t end = do_b ? n_total : n_a;
-  const int64_t n4 = end / 4;
+// Adam over one brick's five segments (blockIdx.y = brick), two float4 groups per
+// thread and iteration (independent loads in flight); F and the decoder (segments
+// 0-3) also refresh their BF16 shadow.  With `sched`, the brick's plateau scale
+// multiplies both learning rates, a finished brick is left alone, and G is updated
+// when the brick's density decision says so, with its own bias corrections.
+__global__ void k_adam(AdamLayout lay, float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, uint16_t* __restrict__ shadow, int do_b, float lr_a, float lr_b,
+                       float b1, float b2, float eps, const StepState* st, const BrickSched* sched, float pfactor) {
+  const int b = blockIdx.y;
+  float mult = 1.f, bc1b = st->bc1b, rbc2b = st->rbc2b;
+  bool den = do_b != 0;
+  if (sched) {
+    const BrickSched& q = sched[b];
+    if (q.finished) return;
+    for (int k = 0; k < q.plateaus; ++k) mult *= pfactor;
+    den = q.den_on != 0;
+    bc1b = q.bc1b;
+    rbc2b = q.rbc2b;
+  }
+  const float bc1a = st->bc1a, rbc2a = st->rbc2a;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  float4* P4 = reinterpret_cast<float4*>(p);
-  const float4* G4 = reinterpret_cast<const float4*>(g);
-  float4* M4 = reinterpret_cast<float4*>(m);
-  float4* V4 = reinterpret_cast<float4*>(v);
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += 2 * stride) {
-    const int64_t q2 = q + stride;
-    const bool two = q2 < n4;
-    float4 P = P4[q], Mm = M4[q], V = V4[q];
-    const float4 Gd = G4[q];
-    float4 Pb = make_float4(0.f, 0.f, 0.f, 0.f), Mb = Pb, Vb = Pb, Gb = Pb;
-    if (two) { Pb = P4[q2]; Mb = M4[q2]; Vb = V4[q2]; Gb = G4[q2]; }
-    // n_a is a multiple of 64, so a float4 never straddles the groups
-    const bool a = 4 * q < n_a, ab = 4 * q2 < n_a;
-    adam4(P, Gd, Mm, V, a ? lr_a : lr_b, b1, b2, eps, a ? bc1a : bc1b, a ? rbc2a : rbc2b);
-    P4[q] = P; M4[q] = Mm; V4[q] = V;
-    if (shadow && a) reinterpret_cast<uint2*>(shadow)[q] = make_uint2(pack_bf16(P.x, P.y), pack_bf16(P.z, P.w));
-    if (two) {
-      adam4(Pb, Gb, Mb, Vb, ab ? lr_a : lr_b, b1, b2, eps, ab ? bc1a : bc1b, ab ? rbc2a : rbc2b);
-      P4[q2] = Pb; M4[q2] = Mb; V4[q2] = Vb;
-      if (shadow && ab) reinterpret_cast<uint2*>(shadow)[q2] = make_uint2(pack_bf16(Pb.x, Pb.y), pack_bf16(Pb.z, Pb.w));
+  for (int sgm = 0; sgm < 5; ++sgm) {
+    const bool a = sgm < 4;
+    if (!a && !den) break;
+    const int64_t base = lay.off[sgm] + (int64_t)b * lay.size[sgm];   // a multiple of 64
+    const int64_t n4 = lay.size[sgm] / 4;
+    float4* P4 = reinterpret_cast<float4*>(p + base);
+    const float4* G4 = reinterpret_cast<const float4*>(g + base);
+    float4* M4 = reinterpret_cast<float4*>(m + base);
+    float4* V4 = reinterpret_cast<float4*>(v + base);
+    uint2* S2 = (shadow && a) ? reinterpret_cast<uint2*>(shadow + base) : nullptr;
+    const float lr = (a ? lr_a : lr_b) * mult, bc1 = a ? bc1a : bc1b, rbc2 = a ? rbc2a : rbc2b;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += 2 * stride) {
+      const int64_t q2 = q + stride;
+      const bool two = q2 < n4;
+      float4 P = P4[q], Mm = M4[q], V = V4[q];
+      const float4 Gd = G4[q];
+      float4 Pb = make_float4(0.f, 0.f, 0.f, 0.f), Mb = Pb, Vb = Pb, Gb = Pb;
+      if (two) { Pb = P4[q2]; Mb = M4[q2]; Vb = V4[q2]; Gb = G4[q2]; }
+      adam4(P, Gd, Mm, V, lr, b1, b2, eps, bc1, rbc2);
+      P4[q] = P; M4[q] = Mm; V4[q] = V;
+      if (S2) S2[q] = make_uint2(pack_bf16(P.x, P.y), pack_bf16(P.z, P.w));
+      if (two) {
+        adam4(Pb, Gb, Mb, Vb, lr, b1, b2, eps, bc1, rbc2);
+        P4[q2] = Pb; M4[q2] = Mb; V4[q2] = Vb;
+        if (S2) S2[q2] = make_uint2(pack_bf16(Pb.x, Pb.y), pack_bf16(Pb.z, Pb.w));
+      }
     }
   }
+}
+
+// One thread per brick, after Adam: this iteration's losses update the plateau test
+// (Sec. 5.2: L_rec not reduced by a relative `prel` for more than `pwin` iterations
+// multiplies the learning rates by `pfactor`; the `pmax`-th time finishes the brick)
+// and, if G was trained, the early-stop test (Sec. 4.3.2: the mean of L_den over the
+// last `window` density iterations has not dropped by a relative `rel` below the mean
+// of the window before); then the decisions for the next iteration are taken (G is
+// trained after `delay` iterations, until early stop or `frac` of `total`).
+__global__ void k_schedule(int B, BrickSched* __restrict__ s, double* __restrict__ ring,
+                           const double* __restrict__ losses, SchedParams p, float b1, float b2) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  BrickSched q = s[b];
+  if (!q.finished) {
+    const double L = losses[4 * b + 0];
+    if (q.it == 0 || L < q.best * (1.0 - (double)p.prel)) {
+      q.best = L;
+      q.bad = 0;
+    } else {
+      q.bad += 1;
+    }
+    if (q.bad > p.pwin) {
+      q.plateaus += 1;
+      q.bad = 0;
+      if (q.plateaus >= p.pmax) q.finished = 1;
+    }
+    if (q.den_on) {
+      const double x = losses[4 * b + 1];
+      double* rg = ring + (int64_t)b * 2 * kMaxDensityWindow;
+      const int W = p.window, i = q.den_n % (2 * W), j = (q.den_n + W) % (2 * W);
+      const double old2 = q.den_n >= 2 * W ? rg[i] : 0.0;   // value of density iteration den_n - 2W
+      const double old1 = q.den_n >= W ? rg[j] : 0.0;       // value of density iteration den_n - W
+      q.s_cur += x - old1;
+      q.s_prev += old1 - old2;
+      rg[i] = x;
+      q.den_n += 1;
+      if (q.den_n >= 2 * W) {
+        const double now = q.s_cur / W, before = q.s_prev / W;
+        if (!(now < before - (double)p.rel * fabs(before))) q.den_stopped = 1;
+      }
+    }
+  }
+  q.it += 1;
+  const long long next = q.it + 1;
+  q.den_on = !q.finished && !q.den_stopped && next > p.delay && (double)next <= (double)p.frac * (double)p.total;
+  if (q.den_on) {
+    const int t = q.den_n + 1;
+    q.bc1b = (float)(1.0 - pow((double)b1, t));
+    q.rbc2b = (float)(1.0 / (1.0 - pow((double)b2, t)));
+  }
+  s[b] = q;
 }
 
 // BF16 shadow of the first n parameters (n a multiple of 4).
@@ -422,16 +494,23 @@ cudaError_t launch_finalize(const Launch& L, const Bricks& br, const Model& md, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_adam(const Launch& L, float* p, float* g, float* m, float* v, uint16_t* shadow,
-                        int64_t n_a, int64_t n_total, bool do_b, float lr_a, float lr_b,
-                        float beta1, float beta2, float eps, StepState* st) {
+cudaError_t launch_adam(const Launch& L, const AdamLayout& lay, float* p, float* g, float* m, float* v,
+                        uint16_t* shadow, bool do_b, float lr_a, float lr_b, float beta1, float beta2, float eps,
+                        StepState* st, const BrickSched* sched, float pfactor) {
   k_advance<<<1, 1, 0, L.stream>>>(st, do_b ? 1 : 0, beta1, beta2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int64_t n = (do_b ? n_total : n_a) / 4;
-  k_adam<<<blocks_for(n, 256, L.num_sms, 8), 256, 0, L.stream>>>(p, g, m, v, shadow, n_a, n_total,
-                                                                 do_b ? 1 : 0, lr_a, lr_b, beta1,
-                                                                 beta2, eps, st);
+  const int64_t per_brick = (lay.size[0] + lay.size[1] + lay.size[2] + lay.size[3] + lay.size[4]) / 4;
+  const int bx = (int)std::max<int64_t>(1, std::min<int64_t>((per_brick + 511) / 512,
+                                                             (int64_t)8 * L.num_sms / lay.n_bricks + 1));
+  k_adam<<<dim3(bx, lay.n_bricks), 256, 0, L.stream>>>(lay, p, g, m, v, shadow, do_b ? 1 : 0, lr_a, lr_b, beta1,
+                                                       beta2, eps, st, sched, pfactor);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schedule(const Launch& L, int n_bricks, BrickSched* s, double* ring, const double* losses,
+                            const SchedParams& p, float beta1, float beta2) {
+  k_schedule<<<1, 64, 0, L.stream>>>(n_bricks, s, ring, losses, p, beta1, beta2);
   return cudaGetLastError();
 }
 

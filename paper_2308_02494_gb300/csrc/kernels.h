@@ -48,9 +48,41 @@ struct StepState {
   float bc1b, rbc2b;         // the same for t_b
   double p1a, p2a, p1b, p2b; // beta1^t_a, beta2^t_a, beta1^t_b, beta2^t_b (running products)
 };
-cudaError_t launch_adam(const Launch& L, float* p, float* g, float* m, float* v, uint16_t* shadow,
-                        int64_t n_a, int64_t n_total, bool do_b, float lr_a, float lr_b,
-                        float beta1, float beta2, float eps, StepState* st);
+// The training routine of Sec. 4.3.2 (delayed start and early stop of the transform
+// updates) and the plateau scheduler of Sec. 5.2, kept per brick on the device.
+constexpr int kMaxDensityWindow = 4096;
+struct BrickSched {
+  long long it;               // iterations this brick has trained
+  int plateaus, bad;          // plateau reductions so far; iterations without improvement
+  int finished;               // no further updates (the last plateau fired)
+  int den_on;                 // G is updated at the next iteration
+  int den_stopped;            // early stop (or the iteration cutoff) has fired
+  int den_n;                  // density iterations so far
+  double best;                // lowest L_rec of the plateau test
+  double s_cur, s_prev;       // sums of L_den over the last and the previous window
+  float bc1b, rbc2b;          // Adam bias corrections of G for the next density iteration
+};
+struct SchedParams {
+  int delay, window;
+  float rel, frac;
+  long long total;
+  int pwin;
+  float prel, pfactor;
+  int pmax;
+};
+cudaError_t launch_schedule(const Launch& L, int n_bricks, BrickSched* s, double* ring, const double* losses,
+                            const SchedParams& p, float beta1, float beta2);
+
+// Adam, one grid row of CTAs per brick over the brick's five parameter segments
+// (F, W1, W2, w3, G).  With `sched`, a brick's learning rates take its plateau scale,
+// a finished brick is skipped, and G follows the brick's density decision.
+struct AdamLayout {
+  int64_t off[5], size[5];    // segment offsets and per-brick strides (floats)
+  int n_bricks;
+};
+cudaError_t launch_adam(const Launch& L, const AdamLayout& lay, float* p, float* g, float* m, float* v,
+                        uint16_t* shadow, bool do_b, float lr_a, float lr_b, float beta1, float beta2, float eps,
+                        StepState* st, const BrickSched* sched, float pfactor);
 cudaError_t launch_shadow(const Launch& L, const float* p, uint16_t* shadow, int64_t n);
 
 // Sampler (Philox + Morton counting sort) and ground-truth lookup.

@@ -82,6 +82,7 @@ void make_layout(const srn_config* c, srn_layout* L) {
 // Workspace carving (every piece 256-byte aligned).
 struct WsLayout {
   size_t state, acc, gsum, rho, herr, sort_tmp, sort_rank, sort_hist, feat, dfeat, ustart, tiles, tile_ctr;
+  size_t sched, sring;
   size_t r_loc, r_rank, r_bid, r_pos, r_xyz, r_val, r_cnt, r_off, total;
 };
 
@@ -105,7 +106,9 @@ WsLayout ws_layout(const srn_config* c, int64_t maxp) {
   const int64_t max_tiles = (int64_t)c->n_bricks * (srn::kUnits + 1) + maxp / 1024 + 1;
   w.ustart = o; o += bf16 ? align256(sizeof(int32_t) * (srn::kUnits + 1) * c->n_bricks) : 0;
   w.tiles = o; o += bf16 ? align256(sizeof(srn::ScatTile) * max_tiles) : 0;
-  w.tile_ctr = o; o += align256(sizeof(int32_t) * 2);
+  w.tile_ctr = o; o += align256(sizeof(int32_t) * 4);
+  w.sched = o; o += align256(sizeof(srn::BrickSched) * c->n_bricks);
+  w.sring = o; o += align256(sizeof(double) * 2 * srn::kMaxDensityWindow * c->n_bricks);
   w.r_loc = o; o += align256(sizeof(float) * 3 * maxp);
   w.r_rank = o; o += align256(sizeof(uint32_t) * maxp);
   w.r_bid = o; o += align256(sizeof(uint32_t) * maxp);
@@ -152,6 +155,9 @@ struct srn_handle {
   WsLayout wl;
   int num_sms;
   std::vector<GraphEntry> graphs;
+  // training routine (srn_set_schedule)
+  bool has_sched = false;
+  srn_schedule sched_cfg{};
   // measurement hook: a ring of event pairs around the query pass or one of its kernels
   int32_t timing = SRN_TIME_OFF;
   std::vector<cudaEvent_t> ev_start, ev_stop;
@@ -161,6 +167,13 @@ struct srn_handle {
   int64_t timed_launches = 0;
 
   srn::StepState* state() const { return reinterpret_cast<srn::StepState*>(ws + wl.state); }
+  srn::BrickSched* sched() const { return reinterpret_cast<srn::BrickSched*>(ws + wl.sched); }
+  double* sring() const { return reinterpret_cast<double*>(ws + wl.sring); }
+  srn::SchedParams sched_params() const {
+    const srn_schedule& c = sched_cfg;
+    return srn::SchedParams{c.delay_iters, c.density_window, c.density_rel, c.density_frac, c.total_iters,
+                            c.plateau_window, c.plateau_rel, c.plateau_factor, c.plateau_max};
+  }
   int32_t* status() const { return reinterpret_cast<int32_t*>(ws + wl.state + sizeof(srn::StepState)); }
   srn::TrainWs train_ws() const {
     srn::TrainWs w;
@@ -175,6 +188,7 @@ struct srn_handle {
     w.ustart = reinterpret_cast<int32_t*>(ws + wl.ustart);
     w.tiles = reinterpret_cast<srn::ScatTile*>(ws + wl.tiles);
     w.tile_ctr = reinterpret_cast<int32_t*>(ws + wl.tile_ctr);
+    w.sched = nullptr;
     return w;
   }
   srn::Model model() const {
@@ -235,12 +249,14 @@ srn_status check_training_counts(const srn::Bricks& br) {
 }
 
 srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn::Bricks& br,
-                     const float* xyz, const float* target, float* out, int upstream = 0) {
+                     const float* xyz, const float* target, float* out, int upstream = 0,
+                     const srn::BrickSched* sched = nullptr) {
   const srn::Launch L = h->launch(stream);
   const srn::Model md = h->model();
   const srn::Grads gr = h->grads();
   srn::TrainWs ws = h->train_ws();
   ws.upstream = upstream;
+  ws.sched = sched;
   size_t slot = 0;
   bool timed = false;
   const bool bf16_train = h->cfg.precision == SRN_BF16 && mode != srn::kForward;
@@ -284,21 +300,26 @@ srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn
 srn_status do_backward(srn_handle* h, void* stream, const float* xyz, const float* target,
                        const srn::Bricks& br, uint32_t flags, double* losses) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool dens = (flags & SRN_DENSITY) != 0;
+  // with the training routine, the density passes always run and each brick follows
+  // its device-side decision
+  const srn::BrickSched* sched = (flags & SRN_SCHEDULE) ? h->sched() : nullptr;
+  const bool dens = (flags & SRN_DENSITY) != 0 || sched;
   cudaError_t e = cudaMemsetAsync(h->t.grads_dev, 0, sizeof(float) * h->lay.n_params, s);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(h->ws + h->wl.acc, 0, h->wl.gsum - h->wl.acc + sizeof(double) * 13 * h->cfg.n_grids * h->cfg.n_bricks, s);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   srn_status st = run_query(h, stream, dens ? srn::kTrainDensity : srn::kTrain, br, xyz, target,
-                            nullptr, (flags & SRN_UPSTREAM) ? 1 : 0);
+                            nullptr, (flags & SRN_UPSTREAM) ? 1 : 0, sched);
   if (st != SRN_OK) return st;
   const srn::Launch L = h->launch(stream);
   const srn::Model md = h->model();
+  srn::TrainWs tws = h->train_ws();
+  tws.sched = sched;
   if (dens) {
-    e = srn::launch_density(L, md, br, h->train_ws(), xyz, h->cfg.density_eps);
+    e = srn::launch_density(L, md, br, tws, xyz, h->cfg.density_eps);
     if (e != cudaSuccess) return cuda_fail(e, "density kernels");
   }
-  e = srn::launch_finalize(L, br, md, h->train_ws(), dens, h->t.grads_dev + h->lay.off_G,
+  e = srn::launch_finalize(L, br, md, tws, dens, h->t.grads_dev + h->lay.off_G,
                            h->lay.size_G, losses);
   if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
   return SRN_OK;
@@ -306,10 +327,18 @@ srn_status do_backward(srn_handle* h, void* stream, const float* xyz, const floa
 
 srn_status do_step(srn_handle* h, void* stream, uint32_t flags) {
   const srn_config& c = h->cfg;
-  cudaError_t e = srn::launch_adam(h->launch(stream), h->t.params_dev, h->t.grads_dev, h->t.adam_m_dev,
+  const srn_layout& ly = h->lay;
+  srn::AdamLayout al{};
+  const int64_t off[5] = {ly.off_F, ly.off_W1, ly.off_W2, ly.off_w3, ly.off_G};
+  const int64_t size[5] = {ly.size_F, ly.size_W1, ly.size_W2, ly.size_w3, ly.size_G};
+  for (int k = 0; k < 5; ++k) { al.off[k] = off[k]; al.size[k] = size[k]; }
+  al.n_bricks = c.n_bricks;
+  const bool sch = (flags & SRN_SCHEDULE) != 0;
+  cudaError_t e = srn::launch_adam(h->launch(stream), al, h->t.params_dev, h->t.grads_dev, h->t.adam_m_dev,
                                    h->t.adam_v_dev, c.precision == SRN_BF16 ? h->t.shadow_dev : nullptr,
-                                   h->lay.n_group_a, h->lay.n_params, (flags & SRN_DENSITY) != 0,
-                                   c.lr_feat, c.lr_xform, c.beta1, c.beta2, c.adam_eps, h->state());
+                                   (flags & SRN_DENSITY) != 0, c.lr_feat, c.lr_xform, c.beta1, c.beta2,
+                                   c.adam_eps, h->state(), sch ? h->sched() : nullptr,
+                                   sch ? h->sched_cfg.plateau_factor : 1.f);
   if (e != cudaSuccess) return cuda_fail(e, "adam kernel");
   return SRN_OK;
 }
@@ -345,7 +374,13 @@ srn_status enqueue_train_step(srn_handle* h, void* stream, uint64_t seed, const 
   if (e != cudaSuccess) return cuda_fail(e, "target lookup");
   srn_status st = do_backward(h, stream, xyz, target, br, flags, losses);
   if (st != SRN_OK) return st;
-  return do_step(h, stream, flags);
+  if ((st = do_step(h, stream, flags)) != SRN_OK) return st;
+  if (flags & SRN_SCHEDULE) {
+    e = srn::launch_schedule(L, h->cfg.n_bricks, h->sched(), h->sring(), losses, h->sched_params(), h->cfg.beta1,
+                             h->cfg.beta2);
+    if (e != cudaSuccess) return cuda_fail(e, "schedule kernel");
+  }
+  return SRN_OK;
 }
 
 }  // namespace
@@ -546,7 +581,11 @@ srn_status srn_train_step(srn_handle* h, void* stream, uint64_t seed, const floa
   if ((s = check_training_counts(br)) != SRN_OK) return s;
   if ((s = make_boxes(h, dims, boxes, &vb)) != SRN_OK) return s;
   if (!vol || !xyz || !target) return fail(SRN_ERR_INVALID_ARG, "volume, xyz or target is NULL");
-  if (flags & ~SRN_DENSITY) return fail(SRN_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  if (flags & ~(SRN_DENSITY | SRN_SCHEDULE)) return fail(SRN_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  if (flags & SRN_SCHEDULE) {
+    if (!h->has_sched) return fail(SRN_ERR_STATE, "SRN_SCHEDULE before srn_set_schedule");
+    if (!losses) return fail(SRN_ERR_INVALID_ARG, "SRN_SCHEDULE needs losses_dev");
+  }
   if (stream == nullptr)
     return enqueue_train_step(h, stream, seed, vol, dims, vb, br, flags, xyz, target, losses);
 
@@ -592,21 +631,77 @@ srn_status srn_train_step(srn_handle* h, void* stream, uint64_t seed, const floa
 }
 
 namespace {
-// Training state as srn_save_state writes it.
+// Training state as srn_save_state writes it: this header, then the per-brick
+// routine state [B] and the L_den history [B][2 kMaxDensityWindow].
 struct StateBlob {
   uint32_t magic;      // 'SRNS'
   uint32_t version;
   int32_t n_bricks, n_grids;
+  int32_t has_sched, pad;
+  srn_schedule sched_cfg;
   srn::StepState st;
 };
-constexpr uint32_t kStateMagic = 0x534e5253u, kStateVersion = 1;
+constexpr uint32_t kStateMagic = 0x534e5253u, kStateVersion = 2;
+size_t sched_bytes(const srn_handle* h) { return sizeof(srn::BrickSched) * h->cfg.n_bricks; }
+size_t ring_bytes(const srn_handle* h) { return sizeof(double) * 2 * srn::kMaxDensityWindow * h->cfg.n_bricks; }
 }  // namespace
 
 srn_status srn_state_bytes(srn_handle* h, size_t* bytes) {
   srn_status s = check_handle(h);
   if (s != SRN_OK) return s;
   if (!bytes) return fail(SRN_ERR_INVALID_ARG, "NULL argument");
-  *bytes = sizeof(StateBlob);
+  *bytes = sizeof(StateBlob) + sched_bytes(h) + ring_bytes(h);
+  return SRN_OK;
+}
+
+srn_status srn_set_schedule(srn_handle* h, const srn_schedule* c) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (!c) return fail(SRN_ERR_INVALID_ARG, "NULL schedule");
+  if (c->delay_iters < 0 || c->density_window < 1 || c->density_window > srn::kMaxDensityWindow ||
+      c->total_iters < 1 || c->plateau_window < 1 || c->plateau_max < 1 || !(c->density_rel > 0.f) ||
+      !(c->density_frac > 0.f && c->density_frac <= 1.f) || !(c->plateau_rel > 0.f) ||
+      !(c->plateau_factor > 0.f && c->plateau_factor <= 1.f))
+    return fail(SRN_ERR_INVALID_ARG, "bad training-routine setting");
+  // every brick at iteration 0; the decision for iteration 1 as k_schedule would take it
+  std::vector<srn::BrickSched> init(h->cfg.n_bricks);
+  for (auto& q : init) {
+    q = srn::BrickSched{};
+    q.den_on = 1 > c->delay_iters && 1.0 <= (double)c->density_frac * (double)c->total_iters;
+    q.bc1b = (float)(1.0 - h->cfg.beta1);
+    q.rbc2b = (float)(1.0 / (1.0 - h->cfg.beta2));
+  }
+  cudaError_t e = cudaMemcpy(h->sched(), init.data(), sched_bytes(h), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->sring(), 0, ring_bytes(h));
+  if (e != cudaSuccess) return cuda_fail(e, "schedule init");
+  h->sched_cfg = *c;
+  h->has_sched = true;
+  return SRN_OK;
+}
+
+srn_status srn_read_schedule(srn_handle* h, void* stream, srn_brick_schedule* out) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (!out) return fail(SRN_ERR_INVALID_ARG, "NULL output");
+  if (!h->has_sched) return fail(SRN_ERR_STATE, "no training routine set");
+  std::vector<srn::BrickSched> q(h->cfg.n_bricks);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(q.data(), h->sched(), sched_bytes(h), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_fail(e, "schedule read");
+  for (int b = 0; b < h->cfg.n_bricks; ++b) {
+    srn_brick_schedule& o = out[b];
+    o.iteration = q[b].it;
+    o.plateaus = q[b].plateaus;
+    float sc = 1.f;
+    for (int k = 0; k < q[b].plateaus; ++k) sc *= h->sched_cfg.plateau_factor;
+    o.lr_scale = sc;
+    o.finished = q[b].finished;
+    o.density_on = q[b].den_on;
+    o.density_stopped = q[b].den_stopped;
+    o.density_iters = q[b].den_n;
+    o.best_rec = q[b].best;
+  }
   return SRN_OK;
 }
 
@@ -615,16 +710,26 @@ srn_status srn_save_state(srn_handle* h, void* stream, void* dst, size_t bytes) 
   if (s != SRN_OK) return s;
   if (!dst) return fail(SRN_ERR_INVALID_ARG, "NULL destination");
   if (bytes < sizeof(StateBlob)) return fail(SRN_ERR_INVALID_ARG, "state buffer of %zu bytes < %zu", bytes, sizeof(StateBlob));
+  size_t need = 0;
+  srn_state_bytes(h, &need);
+  if (bytes < need) return fail(SRN_ERR_INVALID_ARG, "state buffer of %zu bytes < %zu", bytes, need);
   StateBlob b{};
   b.magic = kStateMagic;
   b.version = kStateVersion;
   b.n_bricks = h->cfg.n_bricks;
   b.n_grids = h->cfg.n_grids;
+  b.has_sched = h->has_sched ? 1 : 0;
+  b.sched_cfg = h->sched_cfg;
+  unsigned char* out = static_cast<unsigned char*>(dst);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(&b.st, h->state(), sizeof(srn::StepState), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out + sizeof b, h->sched(), sched_bytes(h), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out + sizeof b + sched_bytes(h), h->sring(), ring_bytes(h), cudaMemcpyDeviceToHost, cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e != cudaSuccess) return cuda_fail(e, "state read");
-  std::memcpy(dst, &b, sizeof b);
+  std::memcpy(out, &b, sizeof b);
   return SRN_OK;
 }
 
@@ -632,17 +737,27 @@ srn_status srn_load_state(srn_handle* h, void* stream, const void* src, size_t b
   srn_status s = check_handle(h);
   if (s != SRN_OK) return s;
   if (!src) return fail(SRN_ERR_INVALID_ARG, "NULL source");
-  if (bytes < sizeof(StateBlob)) return fail(SRN_ERR_INVALID_ARG, "state buffer of %zu bytes < %zu", bytes, sizeof(StateBlob));
+  size_t need = 0;
+  srn_state_bytes(h, &need);
+  if (bytes < sizeof(StateBlob)) return fail(SRN_ERR_INVALID_ARG, "state buffer of %zu bytes < %zu", bytes, need);
   StateBlob b;
   std::memcpy(&b, src, sizeof b);
   if (b.magic != kStateMagic || b.version != kStateVersion) return fail(SRN_ERR_INVALID_ARG, "not a training state of this build");
+  if (bytes < need) return fail(SRN_ERR_INVALID_ARG, "state buffer of %zu bytes < %zu", bytes, need);
   if (b.n_bricks != h->cfg.n_bricks || b.n_grids != h->cfg.n_grids)
     return fail(SRN_ERR_INVALID_ARG, "training state of %d bricks x %d grids, handle has %d x %d", b.n_bricks,
                 b.n_grids, h->cfg.n_bricks, h->cfg.n_grids);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const unsigned char* in = static_cast<const unsigned char*>(src);
   cudaError_t e = cudaMemcpyAsync(h->state(), &b.st, sizeof(srn::StepState), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->sched(), in + sizeof b, sched_bytes(h), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->sring(), in + sizeof b + sched_bytes(h), ring_bytes(h), cudaMemcpyHostToDevice, cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e != cudaSuccess) return cuda_fail(e, "state write");
+  h->has_sched = b.has_sched != 0;
+  h->sched_cfg = b.sched_cfg;
   return SRN_OK;
 }
 

@@ -132,10 +132,23 @@ class SRN:
                              np.asarray(boxes).ravel(), xyz.data_ptr(), offsets, target.data_ptr())
         return target
 
-    def train_step(self, seed, volume, boxes, offsets, density, xyz, target, stream=None):
+    def set_schedule(self, delay_iters=500, density_window=1000, density_rel=1e-4, density_frac=0.8,
+                     total_iters=50000, plateau_window=500, plateau_rel=1e-4, plateau_factor=0.1,
+                     plateau_max=3) -> None:
+        """The paper's training routine (Sec. 4.3.2 and 5.2), applied on the device by
+        train_step(..., schedule=True); defaults are the paper's values."""
+        _s.srn_set_schedule(self.handle, _s.Schedule(delay_iters, density_window, density_rel, density_frac,
+                                                     total_iters, plateau_window, plateau_rel, plateau_factor,
+                                                     plateau_max))
+
+    def read_schedule(self, stream=None) -> list:
+        return _s.srn_read_schedule(self.handle, _stream_ptr(stream), self.n_bricks)
+
+    def train_step(self, seed, volume, boxes, offsets, density, xyz, target, stream=None, schedule=False):
         dims = [volume.shape[2], volume.shape[1], volume.shape[0]]
+        flags = _s.SRN_SCHEDULE if schedule else (_s.SRN_DENSITY if density else 0)
         _s.srn_train_step(self.handle, _stream_ptr(stream), seed, volume.data_ptr(), dims,
-                          np.asarray(boxes).ravel(), offsets, _s.SRN_DENSITY if density else 0,
+                          np.asarray(boxes).ravel(), offsets, flags,
                           xyz.data_ptr(), target.data_ptr(), self.losses.data_ptr())
         return self.losses
 

@@ -25,6 +25,7 @@ SRN_FP32 = 0
 SRN_BF16 = 1
 SRN_DENSITY = 1
 SRN_UPSTREAM = 2
+SRN_SCHEDULE = 4
 SRN_MAX_BRICKS = 64
 
 # Every symbol include/srn.h declares (checked by the CPU tests).
@@ -33,6 +34,7 @@ EXPORTS = (
     "srn_sync_shadow", "srn_sample_points", "srn_sample_target", "srn_forward", "srn_backward",
     "srn_step", "srn_train_step", "srn_render", "srn_set_timing", "srn_read_timing", "srn_get_status",
     "srn_sample_points_static", "srn_decode", "srn_state_bytes", "srn_save_state", "srn_load_state",
+    "srn_set_schedule", "srn_read_schedule",
 )
 SRN_STATIC_SAMPLER_MAX_POINTS = 131072
 SRN_STATIC_SAMPLER_MAX_BRICKS = 8
@@ -50,6 +52,18 @@ class Config(ct.Structure):
                 ("flat_top_p", ct.c_int32), ("density_eps", ct.c_float), ("lr_feat", ct.c_float),
                 ("lr_xform", ct.c_float), ("beta1", ct.c_float), ("beta2", ct.c_float),
                 ("adam_eps", ct.c_float)]
+
+
+class Schedule(ct.Structure):
+    _fields_ = [("delay_iters", ct.c_int32), ("density_window", ct.c_int32), ("density_rel", ct.c_float),
+                ("density_frac", ct.c_float), ("total_iters", ct.c_int64), ("plateau_window", ct.c_int32),
+                ("plateau_rel", ct.c_float), ("plateau_factor", ct.c_float), ("plateau_max", ct.c_int32)]
+
+
+class BrickSchedule(ct.Structure):
+    _fields_ = [("iteration", ct.c_int64), ("lr_scale", ct.c_float), ("plateaus", ct.c_int32),
+                ("finished", ct.c_int32), ("density_on", ct.c_int32), ("density_stopped", ct.c_int32),
+                ("density_iters", ct.c_int32), ("best_rec", ct.c_double)]
 
 
 class Layout(ct.Structure):
@@ -100,6 +114,8 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
         "srn_sample_points_static": [P, U64, U64, I32, I64P, P],
         "srn_decode": [P, P, ct.POINTER(ct.c_int32), I64P, I64, P],
         "srn_state_bytes": [P, ct.POINTER(ct.c_size_t)],
+        "srn_set_schedule": [P, ct.POINTER(Schedule)],
+        "srn_read_schedule": [P, P, ct.POINTER(BrickSchedule)],
         "srn_save_state": [P, P, P, ct.c_size_t],
         "srn_load_state": [P, P, P, ct.c_size_t],
     }
@@ -207,6 +223,16 @@ def srn_sample_points_static(stream, seed, step, n_bricks, offsets, xyz) -> None
 def srn_decode(h, stream, grid, boxes, vox, out) -> None:
     g = (ct.c_int32 * 3)(*[int(v) for v in grid])
     _check(load().srn_decode(h, stream, g, _i64(boxes), int(vox), out))
+
+
+def srn_set_schedule(h, sched: Schedule) -> None:
+    _check(load().srn_set_schedule(h, ct.byref(sched)))
+
+
+def srn_read_schedule(h, stream, n_bricks: int) -> list:
+    out = (BrickSchedule * n_bricks)()
+    _check(load().srn_read_schedule(h, stream, out))
+    return [{f: getattr(o, f) for f, _ in BrickSchedule._fields_} for o in out]
 
 
 def srn_state_bytes(h) -> int:
