@@ -457,8 +457,8 @@ constexpr int NCAP = 1024;      // nodes of a usable box
 // Shared memory of k_scat (dynamic): per-point data, the counting sort, per-cell
 // corner sums (corner-major, conflict-free) and the carried partial sums.
 struct ScatSmem {
-  float cs[16][CCAP];          // corner k, channel e -> cs[k*C + e][cell]
-  float pl[16][SNT];           // chunk t's last partial sum when its cell goes on past the chunk
+  float cs[16 * CCAP];         // per-cell corner sums: corner k, cell l, channel e at (k CCAP + l) C + e
+  float pl[16 * SNT];          // chunk t's last partial sums (its cell goes on past the chunk): (k SNT + t) C + e
   uint2 tbox[kMaxGrids];       // the tile's node box in every grid (lo and node counts, bytes)
   float4 wg[ST];               // per point: grid coordinates s (Eq. 2), then, for the points of a
                                // box pass, the cell weights; .w holds dL/dy (bf16 x 2 bits)
@@ -526,17 +526,33 @@ __device__ __forceinline__ void add_corners(float (&a)[8][C], const float4 v) {
 // pl[.][t]; the chunk's first run, when its cell began in an earlier chunk, is that
 // cell's last piece, and this thread adds the parked pieces of the cell's earlier
 // chunks to it and stores the sum.
+// Corner k's C sums of cell l (a float2 when C = 2) in the layouts of ScatSmem.
+template <int C>
+__device__ __forceinline__ void put_sums(float* base, int k, int l, int cap, const float (&a)[8][C]) {
+  if (C == 2) *reinterpret_cast<float2*>(base + ((k * cap + l) << 1)) = make_float2(a[k][0], a[k][C - 1]);
+  else base[k * cap + l] = a[k][0];
+}
+template <int C>
+__device__ __forceinline__ void add_sums(const float* base, int k, int l, int cap, float (&a)[8][C]) {
+  if (C == 2) {
+    const float2 v = *reinterpret_cast<const float2*>(base + ((k * cap + l) << 1));
+    a[k][0] += v.x;
+    a[k][C - 1] += v.y;
+  } else {
+    a[k][0] += base[k * cap + l];
+  }
+}
+
 template <int C>
 __device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const short (&id)[PPT],
                          const int (&rk)[PPT]) {
-  constexpr int NV = 8 * C;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncx = bx.n[0] - 1, ncy = bx.n[1] - 1, ncz = bx.n[2] - 1, ncells = bx.ncells;
   {  // cells without points must read as zero in the gather
-    const int n4 = (ncells + 3) >> 2;
+    const int n4 = (ncells * C + 3) >> 2;   // float4 per corner row
     for (int l = tid; l < n4; l += SNT)
 #pragma unroll
-      for (int r = 0; r < NV; ++r) reinterpret_cast<float4*>(s.cs[r])[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < 8; ++k) reinterpret_cast<float4*>(s.cs + k * CCAP * C)[l] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();   // the callers took every point's rank in its cell (s.cnt) before
   {  // block-wide exclusive scan, two consecutive cells per thread
@@ -593,9 +609,7 @@ __device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const sh
         if (u > 0 && cel[u] != cur) {   // cell cur ended inside the chunk
           if (first && start0 < q0) head_cell = cur;
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int e = 0; e < C; ++e) s.cs[k * C + e][cur] = a[k][e];
+          for (int k = 0; k < 8; ++k) put_sums<C>(s.cs, k, cur, CCAP, a);
 #pragma unroll
           for (int k = 0; k < 8; ++k)
 #pragma unroll
@@ -608,32 +622,39 @@ __device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const sh
     }
     if (s.cnt[cur + 1] > q0 + 4) {   // the last run goes on into the next chunk
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-#pragma unroll
-        for (int e = 0; e < C; ++e) s.pl[k * C + e][tid] = a[k][e];
+      for (int k = 0; k < 8; ++k) put_sums<C>(s.pl, k, tid, SNT, a);
     } else {
       if (first && start0 < q0) head_cell = cur;
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-#pragma unroll
-        for (int e = 0; e < C; ++e) s.cs[k * C + e][cur] = a[k][e];
+      for (int k = 0; k < 8; ++k) put_sums<C>(s.cs, k, cur, CCAP, a);
     }
     head_from = start0 >> 2;
   }
   __syncthreads();
   if (head_cell >= 0) {   // last piece of a cell spanning chunks head_from .. tid
-    float acc[NV], acc2[NV];   // two chunks per iteration: independent loads in flight
+    float acc[8][C], acc2[8][C];   // two chunks per iteration: independent loads in flight
 #pragma unroll
-    for (int r = 0; r < NV; ++r) { acc[r] = s.cs[r][head_cell]; acc2[r] = 0.f; }
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int e = 0; e < C; ++e) { acc[k][e] = 0.f; acc2[k][e] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) add_sums<C>(s.cs, k, head_cell, CCAP, acc);
     int j = head_from;
     for (; j + 1 < tid; j += 2)
 #pragma unroll
-      for (int r = 0; r < NV; ++r) { acc[r] += s.pl[r][j]; acc2[r] += s.pl[r][j + 1]; }
+      for (int k = 0; k < 8; ++k) {
+        add_sums<C>(s.pl, k, j, SNT, acc);
+        add_sums<C>(s.pl, k, j + 1, SNT, acc2);
+      }
     if (j < tid)
 #pragma unroll
-      for (int r = 0; r < NV; ++r) acc[r] += s.pl[r][j];
+      for (int k = 0; k < 8; ++k) add_sums<C>(s.pl, k, j, SNT, acc);
 #pragma unroll
-    for (int r = 0; r < NV; ++r) s.cs[r][head_cell] = acc[r] + acc2[r];
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int e = 0; e < C; ++e) acc[k][e] += acc2[k][e];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) put_sums<C>(s.cs, k, head_cell, CCAP, acc);
   }
   __syncthreads();
   for (int l = tid; l <= ncells; l += SNT) s.cnt[l] = 0;   // ready for the next pass
@@ -656,8 +677,13 @@ __device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const sh
       const bool in = ((k & 1) ? x1 : x0) && ((k & 2) ? y1 : y0) && ((k & 4) ? z1 : z0);
       if (in) {
         const int l = l0 - ((k & 1) ? 1 : 0) - ((k & 2) ? sy : 0) - ((k & 4) ? sz : 0);
-#pragma unroll
-        for (int e = 0; e < C; ++e) v[e] += s.cs[k * C + e][l];
+        if (C == 2) {
+          const float2 w = *reinterpret_cast<const float2*>(s.cs + ((k * CCAP + l) << 1));
+          v[0] += w.x;
+          v[C - 1] += w.y;
+        } else {
+          v[0] += s.cs[k * CCAP + l];
+        }
       }
     }
     const int64_t g = ((int64_t)(bx.lo[2] + qz) * R + (bx.lo[1] + qy)) * R + bx.lo[0] + qx;
