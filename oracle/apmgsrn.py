@@ -220,7 +220,8 @@ def grad_rec(params: dict, x, v, rnd=None):
     Chain rule written out: f = m (max-min) + min, dL/df = 2 (f - v)/N.
     rnd (see mlp_forward) also rounds the activation-side operand of every
     backward matrix product (dz2, dz1, and the y / ReLU(z1) factors of dW).
-    Returns dict(L_rec, f, h, dF, dW1, dW2, dw3) where h = (f - v)^2 per point."""
+    Returns dict(L_rec, f, h, dF, dW1, dW2, dw3, dy) where h = (f - v)^2 per point
+    and dy = dL/dy [N, M*C]."""
     q = rnd or _ident
     F = np.asarray(params["F"], dtype=np.float64)
     G = np.asarray(params["G"], dtype=np.float64)
@@ -257,7 +258,54 @@ def grad_rec(params: dict, x, v, rnd=None):
             for ch in range(C):   # scatter-add of each point's share into its corner node
                 flat[:, ch] += np.bincount(node, weights=wt[:, ch], minlength=R * R * R)
     return {"L_rec": float(np.mean(r ** 2)), "f": f, "h": r ** 2, "dF": dF,
-            "dW1": dW1, "dW2": dW2, "dw3": dw3}
+            "dW1": dW1, "dW2": dW2, "dw3": dw3, "dy": dy}
+
+
+def interp_grid_du(Fi: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Derivative of Eq. 2 for one grid with respect to the local coordinate u.
+
+    Inside the cell the interpolant is trilinear in w = s - c, so d e / d w_x is the
+    sum over corners of (+1 for dx = 1, -1 for dx = 0) times the other two axes'
+    weights times the corner value, and likewise for y and z; ds/du = (R-1)/2.
+    Outside [-1, 1] the feature is the constant 0, so its derivative is 0.  At a cell
+    face the derivative is the one of the cell chosen by cell_and_weights.
+    Fi [R, R, R, C]; u [N, 3].  Returns [N, C, 3] (last axis: d/du_x, d/du_y, d/du_z)."""
+    res = Fi.shape[0]
+    c, w = cell_and_weights(u, res)
+    out = np.zeros((u.shape[0], Fi.shape[3], 3))
+    for dx, dy, dz in corner_offsets():
+        val = Fi[c[:, 2] + dz, c[:, 1] + dy, c[:, 0] + dx, :]          # [N, C]
+        fx = w[:, 0] if dx else 1.0 - w[:, 0]
+        fy = w[:, 1] if dy else 1.0 - w[:, 1]
+        fz = w[:, 2] if dz else 1.0 - w[:, 2]
+        out[:, :, 0] += ((1.0 if dx else -1.0) * fy * fz)[:, None] * val
+        out[:, :, 1] += ((1.0 if dy else -1.0) * fx * fz)[:, None] * val
+        out[:, :, 2] += ((1.0 if dz else -1.0) * fx * fy)[:, None] * val
+    out *= (res - 1) / 2.0
+    out[~inside_mask(u)] = 0.0
+    return out
+
+
+def grad_transform_through_features(params: dict, x, dy):
+    """Gradient that a loss with dL/dy = dy [N, M*C] sends into the transforms G
+    through the features (Eq. 1 and Eq. 2), with u_i = A_i x + t_i:
+    dL/dA_i = sum_n (dL/du_in) x_n^T and dL/dt_i = sum_n dL/du_in, where
+    dL/du_in = sum_c dy_{n,(i,c)} d e_{i,c} / d u.
+    Sec. 4.3.2 trains G with L_den alone; this is the L_rec part left out there,
+    for diagnostics and for the full gradient of f.  Returns dG [M, 3, 4]."""
+    F = np.asarray(params["F"], dtype=np.float64)
+    G = np.asarray(params["G"], dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    dy = np.asarray(dy, dtype=np.float64)
+    M, C = F.shape[0], F.shape[4]
+    u = local_coords(G, x)
+    dG = np.zeros_like(G)
+    for i in range(M):
+        J = interp_grid_du(F[i], u[:, i, :])                        # [N, C, 3]
+        dLdu = np.einsum("nc,ncd->nd", dy[:, i * C:(i + 1) * C], J)   # [N, 3]
+        dG[i, :, :3] = dLdu.T @ x
+        dG[i, :, 3] = dLdu.sum(axis=0)
+    return dG
 
 
 def grad_density(G, x, h, p: int = 10, eps: float = 1e-8):
