@@ -56,6 +56,11 @@ typedef enum { SRN_FP32 = 0, SRN_BF16 = 1 } srn_precision;
 #define SRN_SCHEDULE 4u  /* srn_train_step only: the training routine set by srn_set_schedule
                             decides, per brick on the device, whether G is trained and the
                             learning-rate scale; SRN_DENSITY is then ignored */
+#define SRN_REC_DG 8u    /* srn_backward only: also the gradient of L_rec (or, with SRN_UPSTREAM,
+                            of the upstream loss) with respect to G through Eq. 1-2, added into
+                            G's gradient.  Sec. 4.3.2 trains G with L_den alone, so training
+                            never sets it: it is the rest of the full gradient of f, for
+                            diagnostics and for autograd through the transforms */
 
 /* Model and optimiser configuration (Sec. 4.1, 4.2, 6).  Supported in this build:
  * hidden = 64; channels in {1, 2}; K = n_grids*channels in {16, 32, 64, 128};
@@ -176,8 +181,9 @@ srn_status srn_forward(srn_handle* h, void* stream, const float* xyz_dev,
  * Sec. 4.3.2), written (not accumulated) into the gradient buffer.  With
  * SRN_UPSTREAM the gradient is instead that of any loss whose dL/df is given.  With
  * SRN_DENSITY it also evaluates L_den (Eq. 7-9, with h(x) = (f(x) - v(x))^2 and the
- * target rho* held constant) and writes its gradient into G (step (2)); without it
- * G's gradient is zero.  losses_dev (device [B][4] float64, may be NULL) receives
+ * target rho* held constant) and writes its gradient into G (step (2)).  With
+ * SRN_REC_DG the gradient of L_rec (or of the upstream loss) through the features
+ * is added into G's gradient; with neither flag G's gradient is zero.  losses_dev (device [B][4] float64, may be NULL) receives
  * per brick (L_rec, L_den, sum of rho over the batch, point count). */
 srn_status srn_backward(srn_handle* h, void* stream, const float* xyz_dev,
                         const float* target_dev, const int64_t* offsets, uint32_t flags,

@@ -61,6 +61,8 @@ struct TrainWs {
   float* herr;      // [N] per-point squared error h(x)
   double* acc;      // [B][kAccPerBrick] float64 accumulators
   double* gsum;     // [B][M][13] float64 sums for dL_den/dG
+  double* rsum;     // [B][M][12] float64 dL/dG through the features (rec_dg), laid out as G
+  int32_t rec_dg;   // 1: accumulate rsum (SRN_REC_DG)
   int32_t* status;  // device status word
   int32_t upstream; // 1: the target slot holds dL/df (no L_rec); 0: MSE against targets
   __nv_bfloat16* Y;   // [N][K] features (BF16 training pass)
@@ -83,6 +85,17 @@ struct ScatTile {
 enum { ACC_SUM_R2 = 0, ACC_SUM_RHO = 1, ACC_C = 2, ACC_LDEN = 3, kAccPerBrick = 4 };
 
 // ------------------------------------------------------------------ Eq. 1 / Eq. 2
+// Derivative of Eq. 2's interpolant with respect to s inside cell c, for the scalar
+// field whose corner values are a[k] (k = dx + 2 dy + 4 dz): along x the four
+// x-edges' differences weighted by the y and z weights, and likewise for y and z.
+__device__ __forceinline__ void trilinear_ds(const float (&a)[8], float wx, float wy, float wz,
+                                             float& dx, float& dy, float& dz) {
+  const float ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
+  dx = az * (ay * (a[1] - a[0]) + wy * (a[3] - a[2])) + wz * (ay * (a[5] - a[4]) + wy * (a[7] - a[6]));
+  dy = az * (ax * (a[2] - a[0]) + wx * (a[3] - a[1])) + wz * (ax * (a[6] - a[4]) + wx * (a[7] - a[5]));
+  dz = ay * (ax * (a[4] - a[0]) + wx * (a[5] - a[1])) + wy * (ax * (a[6] - a[2]) + wx * (a[7] - a[3]));
+}
+
 struct Cell {
   int cx, cy, cz;
   float wx, wy, wz;

@@ -199,6 +199,11 @@ __global__ void k_finalize(Bricks br, Model md, TrainWs ws, int density, float* 
   const double n = (double)(br.off[b + 1] - br.off[b]);
   const double* acc = ws.acc + b * kAccPerBrick;
   if (ws.sched) density = density && ws.sched[b].den_on;
+  if (ws.rec_dg && !density && i < md.M) {   // G's gradient is the part through the features alone
+    const double* r = ws.rsum + ((int64_t)b * md.M + i) * 12;
+    float* d = dG + (int64_t)b * sdG + 12 * i;
+    for (int j = 0; j < 12; ++j) d[j] = (float)r[j];
+  }
   if (density && i < md.M) {
     const float* g = md.G + (int64_t)b * md.sG + 12 * i;
     const double a00 = g[0], a01 = g[1], a02 = g[2], a10 = g[4], a11 = g[5], a12 = g[6];
@@ -211,9 +216,11 @@ __global__ void k_finalize(Bricks br, Model md, TrainWs ws, int density, float* 
     const double* s = ws.gsum + ((int64_t)b * md.M + i) * 13;
     float* d = dG + (int64_t)b * sdG + 12 * i;
     const double cof[3][3] = {{c00, c01, c02}, {c10, c11, c12}, {c20, c21, c22}};
+    const double* rs = ws.rsum + ((int64_t)b * md.M + i) * 12;
+    const double rw = ws.rec_dg ? 1.0 : 0.0;   // plus the part through the features (SRN_REC_DG)
     for (int r = 0; r < 3; ++r) {
-      for (int e = 0; e < 3; ++e) d[4 * r + e] = (float)(cof[r][e] * s[0] - det * s[4 + 3 * r + e]);
-      d[4 * r + 3] = (float)(-det * s[1 + r]);
+      for (int e = 0; e < 3; ++e) d[4 * r + e] = (float)(cof[r][e] * s[0] - det * s[4 + 3 * r + e] + rw * rs[4 * r + e]);
+      d[4 * r + 3] = (float)(-det * s[1 + r] + rw * rs[4 * r + 3]);
     }
   }
   if (i == 0) {

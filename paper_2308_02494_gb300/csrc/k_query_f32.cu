@@ -68,7 +68,8 @@ struct Lay {
   static constexpr int RHO = X + 4 * T;          // [4][T]
   static constexpr int G = RHO + 4 * T;          // [M][12]
   static constexpr int DET = G + kMaxGrids * 12; // [M]
-  static constexpr int FLOATS = DET + kMaxGrids;
+  static constexpr int RG = DET + kMaxGrids;     // [M][12] dL/dG through the features (rec_dg)
+  static constexpr int FLOATS = RG + kMaxGrids * 12;
 };
 
 template <int K, int MODE>
@@ -95,9 +96,12 @@ k_query_f32(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict_
   float* rhos = smf + L::RHO;
   float* gs = smf + L::G;
   float* dets = smf + L::DET;
+  float* rgs = smf + L::RG;
 
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int M = md.M, C = md.C, R = md.R;
+  if (TRAIN && ws.rec_dg)
+    for (int c = tid; c < M * 12; c += NT) rgs[c] = 0.f;
   if (tid == 0) build_tile_map(br, T, tm);
   __syncthreads();
   const int total = tm.first[br.n];
@@ -138,6 +142,11 @@ k_query_f32(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict_
     }
     sum_r2 = 0.0;
     sum_rho = 0.0;
+    if (ws.rec_dg)
+      for (int c = tid; c < M * 12; c += NT) {
+        atomicAdd(ws.rsum + (int64_t)b * M * 12 + c, (double)rgs[c]);
+        rgs[c] = 0.f;
+      }
   };
 
   int cur = -1;
@@ -373,6 +382,54 @@ k_query_f32(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict_
             if (g0 == 0.f && g1 == 0.f) continue;
             scatter_f32(dFb + i * gsz, c, R, C, g0, g1);
           }
+        }
+      }
+      // ---- dL/dG through the features (SRN_REC_DG): dL/du = (R-1)/2 sum_c dL/dy_c de_c/ds
+      // (Eq. 2 differentiated in the cell), then dL/dA_i += dL/du x^T, dL/dt_i += dL/du;
+      // each warp (32 points, one grid at a time) adds its sums into the block's rgs
+      if (ws.rec_dg) {
+        const int p = tid & (T - 1), gsub = tid / T;
+        const float4 pt = xs[p];
+        const float hs = 0.5f * (float)(R - 1);
+        for (int i = gsub; i < M; i += 4) {
+          float du[3] = {0.f, 0.f, 0.f};
+          if (p < np) {
+            float ux, uy, uz;
+            affine(gs + 12 * i, pt.x, pt.y, pt.z, ux, uy, uz);
+            const Cell c = make_cell(ux, uy, uz, R);
+            if (c.inside) {
+              const float g0 = DYs[p * L::KP + i * C];
+              const float g1 = C == 2 ? DYs[p * L::KP + i * C + 1] : 0.f;
+              const float* Fi = Fb + i * gsz;
+              const int64_t nb = ((int64_t)c.cz * R + c.cy) * R + c.cx;
+              float a[8];
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                const int64_t n = nb + (k & 1) + ((k & 2) ? R : 0) + ((k & 4) ? (int64_t)R * R : 0);
+                if (C == 2) {
+                  const float2 f = __ldg(reinterpret_cast<const float2*>(Fi) + n);
+                  a[k] = fmaf(g0, f.x, g1 * f.y);
+                } else {
+                  a[k] = g0 * __ldg(Fi + n);
+                }
+              }
+              trilinear_ds(a, c.wx, c.wy, c.wz, du[0], du[1], du[2]);
+#pragma unroll
+              for (int d = 0; d < 3; ++d) du[d] *= hs;
+            }
+          }
+          float v[12];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            v[4 * d] = du[d] * pt.x; v[4 * d + 1] = du[d] * pt.y; v[4 * d + 2] = du[d] * pt.z; v[4 * d + 3] = du[d];
+          }
+#pragma unroll
+          for (int j = 0; j < 12; ++j)
+#pragma unroll
+            for (int o = 16; o; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+          if ((tid & 31) == 0)
+#pragma unroll
+            for (int j = 0; j < 12; ++j) atomicAdd(rgs + 12 * i + j, v[j]);
         }
       }
       __syncthreads();

@@ -1064,6 +1064,109 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
   }
 }
 
+// =============================================================================== k_rec_dg
+// dL/dG through the features (SRN_REC_DG), from the decoder's dL/dy: per point and
+// grid, dL/du = (R-1)/2 sum_c dL/dy_c de_c/ds (Eq. 2 differentiated inside the cell,
+// on the BF16 features the forward pass read), then dL/dA_i += dL/du x^T and
+// dL/dt_i += dL/du.  Thread (grid tid % M, point group tid / M) sums its points in
+// float32; the block reduces the groups in float64 and adds them per brick.
+constexpr int RT = 128;   // points per tile
+constexpr int RNT = 256;
+
+template <int C>
+__global__ void __launch_bounds__(RNT) k_rec_dg(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
+  __shared__ Bricks br;
+  __shared__ TileMap tm;
+  __shared__ float4 sx[RT];
+  __shared__ float sg[kMaxGrids * 12];
+  __shared__ double red[RNT];
+  load_bricks(brp, br);
+  const int tid = threadIdx.x, M = md.M, R = md.R;
+  const int npg = RNT / M, gi = tid % M, pg = tid / M;   // M divides RNT (M = K / C, a power of two)
+  if (tid == 0) build_tile_map(br, RT, tm);
+  __syncthreads();
+  const int total = tm.first[br.n];
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int tb = blockIdx.x * per, te = min(total, tb + per);
+  const int64_t ntot = br.off[br.n];
+  const int64_t gsz = (int64_t)R * R * R * C;
+  const float hs = 0.5f * (float)(R - 1);
+  float acc[12];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) acc[j] = 0.f;
+  auto flush = [&](int b) {
+    for (int j = 0; j < 12; ++j) {
+      red[tid] = (double)acc[j];
+      acc[j] = 0.f;
+      __syncthreads();
+      if (pg == 0) {
+        double t = 0.0;
+        for (int q = 0; q < npg; ++q) t += red[q * M + gi];
+        atomicAdd(ws.rsum + ((int64_t)b * M + gi) * 12 + j, t);
+      }
+      __syncthreads();
+    }
+  };
+  int cur = -1;
+  for (int tile = tb; tile < te; ++tile) {
+    const int b = brick_of_tile(tm, br.n, tile, cur);
+    if (b != cur) {
+      if (cur >= 0) flush(cur);
+      cur = b;
+      for (int k = tid; k < M * 12; k += RNT) sg[k] = md.G[(int64_t)b * md.sG + k];
+    }
+    const int64_t p0 = br.off[b] + (int64_t)(tile - tm.first[b]) * RT;
+    const int np = (int)min((int64_t)RT, br.off[b + 1] - p0);
+    if (tid < RT) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (tid < np) v = make_float4(xyz[3 * (p0 + tid)], xyz[3 * (p0 + tid) + 1], xyz[3 * (p0 + tid) + 2], 0.f);
+      sx[tid] = v;
+    }
+    __syncthreads();
+    const float* g = sg + 12 * gi;
+    const __nv_bfloat16* Fi = md.F16 + (int64_t)b * md.sF + gi * gsz;
+    for (int p = pg; p < np; p += npg) {
+      const float4 x = sx[p];
+      float ux, uy, uz;
+      affine(g, x.x, x.y, x.z, ux, uy, uz);
+      const Cell c = make_cell(ux, uy, uz, R);
+      if (!c.inside) continue;
+      float g0, g1 = 0.f;
+      if (C == 2) {
+        const float2 d = unpack_bf16(__ldg(reinterpret_cast<const unsigned int*>(ws.dY) + (int64_t)gi * ntot + p0 + p));
+        g0 = d.x;
+        g1 = d.y;
+      } else {
+        g0 = __bfloat162float(ws.dY[(int64_t)gi * ntot + p0 + p]);
+      }
+      const int64_t nb = ((int64_t)c.cz * R + c.cy) * R + c.cx;
+      float a[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int64_t n = nb + (k & 1) + ((k & 2) ? R : 0) + ((k & 4) ? (int64_t)R * R : 0);
+        if (C == 2) {
+          const float2 f = node2(Fi, n);
+          a[k] = fmaf(g0, f.x, g1 * f.y);
+        } else {
+          a[k] = g0 * node1(Fi, n);
+        }
+      }
+      float du[3];
+      trilinear_ds(a, c.wx, c.wy, c.wz, du[0], du[1], du[2]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float q = du[d] * hs;
+        acc[4 * d] = fmaf(q, x.x, acc[4 * d]);
+        acc[4 * d + 1] = fmaf(q, x.y, acc[4 * d + 1]);
+        acc[4 * d + 2] = fmaf(q, x.z, acc[4 * d + 2]);
+        acc[4 * d + 3] += q;
+      }
+    }
+    __syncthreads();
+  }
+  if (cur >= 0) flush(cur);
+}
+
 int occupancy(const void* kern, int threads, size_t smem) {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess || n < 1) n = 1;
@@ -1131,8 +1234,14 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark_stop(2);
-    return cudaSuccess;
   }
+  if (ws.rec_dg) {
+    const int grid = std::min((int)((br.off[br.n] + RT - 1) / RT), 2 * L.num_sms);
+    if (md.C == 2) k_rec_dg<2><<<grid, RNT, 0, L.stream>>>(md, br, ws, xyz);
+    else k_rec_dg<1><<<grid, RNT, 0, L.stream>>>(md, br, ws, xyz);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace

@@ -81,7 +81,7 @@ void make_layout(const srn_config* c, srn_layout* L) {
 
 // Workspace carving (every piece 256-byte aligned).
 struct WsLayout {
-  size_t state, acc, gsum, rho, herr, sort_tmp, sort_rank, sort_hist, feat, dfeat, ustart, tiles, tile_ctr;
+  size_t state, acc, gsum, rsum, rho, herr, sort_tmp, sort_rank, sort_hist, feat, dfeat, ustart, tiles, tile_ctr;
   size_t sched, sring;
   size_t r_loc, r_rank, r_bid, r_pos, r_xyz, r_val, r_cnt, r_off, total;
 };
@@ -92,6 +92,7 @@ WsLayout ws_layout(const srn_config* c, int64_t maxp) {
   w.state = o; o += align256(sizeof(srn::StepState) + 64);
   w.acc = o; o += align256(sizeof(double) * srn::kAccPerBrick * c->n_bricks);
   w.gsum = o; o += align256(sizeof(double) * 13 * c->n_grids * c->n_bricks);
+  w.rsum = o; o += align256(sizeof(double) * 12 * c->n_grids * c->n_bricks);
   w.rho = o; o += align256(sizeof(float) * maxp);
   w.herr = o; o += align256(sizeof(float) * maxp);
   w.sort_tmp = o; o += align256(sizeof(float) * 3 * maxp);
@@ -181,6 +182,8 @@ struct srn_handle {
     w.herr = reinterpret_cast<float*>(ws + wl.herr);
     w.acc = reinterpret_cast<double*>(ws + wl.acc);
     w.gsum = reinterpret_cast<double*>(ws + wl.gsum);
+    w.rsum = reinterpret_cast<double*>(ws + wl.rsum);
+    w.rec_dg = 0;
     w.status = status();
     w.upstream = 0;
     w.Y = reinterpret_cast<__nv_bfloat16*>(ws + wl.feat);
@@ -250,13 +253,14 @@ srn_status check_training_counts(const srn::Bricks& br) {
 
 srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn::Bricks& br,
                      const float* xyz, const float* target, float* out, int upstream = 0,
-                     const srn::BrickSched* sched = nullptr) {
+                     const srn::BrickSched* sched = nullptr, int rec_dg = 0) {
   const srn::Launch L = h->launch(stream);
   const srn::Model md = h->model();
   const srn::Grads gr = h->grads();
   srn::TrainWs ws = h->train_ws();
   ws.upstream = upstream;
   ws.sched = sched;
+  ws.rec_dg = rec_dg;
   size_t slot = 0;
   bool timed = false;
   const bool bf16_train = h->cfg.precision == SRN_BF16 && mode != srn::kForward;
@@ -306,15 +310,17 @@ srn_status do_backward(srn_handle* h, void* stream, const float* xyz, const floa
   const bool dens = (flags & SRN_DENSITY) != 0 || sched;
   cudaError_t e = cudaMemsetAsync(h->t.grads_dev, 0, sizeof(float) * h->lay.n_params, s);
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(h->ws + h->wl.acc, 0, h->wl.gsum - h->wl.acc + sizeof(double) * 13 * h->cfg.n_grids * h->cfg.n_bricks, s);
+    e = cudaMemsetAsync(h->ws + h->wl.acc, 0, h->wl.rsum - h->wl.acc + sizeof(double) * 12 * h->cfg.n_grids * h->cfg.n_bricks, s);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
+  const int rec_dg = (flags & SRN_REC_DG) ? 1 : 0;
   srn_status st = run_query(h, stream, dens ? srn::kTrainDensity : srn::kTrain, br, xyz, target,
-                            nullptr, (flags & SRN_UPSTREAM) ? 1 : 0, sched);
+                            nullptr, (flags & SRN_UPSTREAM) ? 1 : 0, sched, rec_dg);
   if (st != SRN_OK) return st;
   const srn::Launch L = h->launch(stream);
   const srn::Model md = h->model();
   srn::TrainWs tws = h->train_ws();
   tws.sched = sched;
+  tws.rec_dg = rec_dg;
   if (dens) {
     e = srn::launch_density(L, md, br, tws, xyz, h->cfg.density_eps);
     if (e != cudaSuccess) return cuda_fail(e, "density kernels");
@@ -557,7 +563,7 @@ srn_status srn_backward(srn_handle* h, void* stream, const float* xyz, const flo
   if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
   if ((s = check_training_counts(br)) != SRN_OK) return s;
   if (!xyz || !target) return fail(SRN_ERR_INVALID_ARG, "xyz or target is NULL");
-  if (flags & ~(SRN_DENSITY | SRN_UPSTREAM)) return fail(SRN_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  if (flags & ~(SRN_DENSITY | SRN_UPSTREAM | SRN_REC_DG)) return fail(SRN_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
   if ((flags & SRN_DENSITY) && (flags & SRN_UPSTREAM))
     return fail(SRN_ERR_INVALID_ARG, "SRN_DENSITY needs the per-point error, which SRN_UPSTREAM lacks");
   return do_backward(h, stream, xyz, target, br, flags, losses);

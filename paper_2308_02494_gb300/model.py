@@ -109,8 +109,12 @@ class SRN:
         _s.srn_forward(self.handle, _stream_ptr(stream), xyz.data_ptr(), offsets, out.data_ptr())
         return out
 
-    def backward(self, xyz, target, offsets, density: bool = False, upstream: bool = False, stream=None):
-        flags = (_s.SRN_DENSITY if density else 0) | (_s.SRN_UPSTREAM if upstream else 0)
+    def backward(self, xyz, target, offsets, density: bool = False, upstream: bool = False,
+                 rec_dg: bool = False, stream=None):
+        """srn_backward; rec_dg adds the gradient of L_rec (or of the upstream loss) into
+        G through the features (SRN_REC_DG), which training leaves out."""
+        flags = ((_s.SRN_DENSITY if density else 0) | (_s.SRN_UPSTREAM if upstream else 0)
+                 | (_s.SRN_REC_DG if rec_dg else 0))
         _s.srn_backward(self.handle, _stream_ptr(stream), xyz.data_ptr(), target.data_ptr(), offsets,
                         flags, self.losses.data_ptr())
         return self.losses
@@ -206,11 +210,14 @@ class APMGSRNFunction(torch.autograd.Function):
 
     forward runs ``srn_forward``; backward runs ``srn_backward`` with
     ``SRN_UPSTREAM`` (the incoming dL/df per point) and returns the flat
-    gradient for the parameters (no gradient for the coordinates)."""
+    gradient for the parameters (no gradient for the coordinates).  With
+    grad_transforms the G part is the full gradient of f through Eq. 1-2
+    (SRN_REC_DG); without it G's part is zero, as in the paper's training, where
+    only L_den moves G."""
 
     @staticmethod
-    def forward(ctx, xyz, params, model: SRN, offsets):
-        ctx.model, ctx.offsets = model, offsets
+    def forward(ctx, xyz, params, model: SRN, offsets, grad_transforms: bool = False):
+        ctx.model, ctx.offsets, ctx.rec_dg = model, offsets, grad_transforms
         ctx.save_for_backward(xyz)
         return model.forward(xyz, offsets)
 
@@ -218,5 +225,5 @@ class APMGSRNFunction(torch.autograd.Function):
     def backward(ctx, grad_f):
         (xyz,) = ctx.saved_tensors
         g = grad_f.contiguous().to(torch.float32)
-        ctx.model.backward(xyz, g, ctx.offsets, upstream=True)
-        return None, ctx.model.grads.clone(), None, None
+        ctx.model.backward(xyz, g, ctx.offsets, upstream=True, rec_dg=ctx.rec_dg)
+        return None, ctx.model.grads.clone(), None, None, None

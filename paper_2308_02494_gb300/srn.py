@@ -26,6 +26,7 @@ SRN_BF16 = 1
 SRN_DENSITY = 1
 SRN_UPSTREAM = 2
 SRN_SCHEDULE = 4
+SRN_REC_DG = 8
 SRN_MAX_BRICKS = 64
 
 # Every symbol include/srn.h declares (checked by the CPU tests).
