@@ -115,3 +115,88 @@ def render(models, boxes, grid, vox, cam, lut, vmin, vmax, width, height, n_samp
     if pixels is None:
         return out.reshape(height, width, 4)
     return out
+
+
+# ----------------------------------------------------------------------------- progressive rendering
+# Sec. 6 renders progressively: pixels are evaluated in the order of an image
+# hierarchy, in checkerboard fashion, and the image shown after each pass is a
+# bilinear upscale of the finest level evaluated so far, with the pixels already
+# evaluated shown as they are.  The paper gives no formulas; the reading taken:
+#   * level l of the hierarchy holds the pixels (a 2^l, b 2^l), a < ceil(W / 2^l),
+#     b < ceil(H / 2^l); the coarsest level L is the first with 2^L >= max(W, H)
+#     (the single pixel (0, 0));
+#   * the order is level L, then each finer level's pixels that no coarser level
+#     holds (three of every 2 x 2 block: the checkerboard), row by row, left to right;
+#   * after k pixels, the finest complete level l is the finest whose whole grid is
+#     among them; a pixel not yet evaluated takes the bilinear blend of the four
+#     level-l samples around (x / 2^l, y / 2^l), the index clamped to the grid
+#     (constant beyond its last row or column); nothing evaluated gives 0.
+
+
+def hierarchy_levels(width: int, height: int) -> int:
+    """The coarsest level L: the smallest with 2^L >= max(W, H)."""
+    L = 0
+    while (1 << L) < max(width, height):
+        L += 1
+    return L
+
+
+def level_dims(width: int, height: int, l: int):
+    """Columns and rows of level l's grid."""
+    s = 1 << l
+    return -(-width // s), -(-height // s)
+
+
+def hierarchy_order(width: int, height: int) -> list:
+    """Flat pixel indices (y W + x) in progressive order, written from the definition."""
+    L = hierarchy_levels(width, height)
+    order = [0]
+    for l in range(L - 1, -1, -1):
+        s = 1 << l
+        for y in range(0, height, s):
+            for x in range(0, width, s):
+                coarser = (x % (2 * s) == 0) and (y % (2 * s) == 0)
+                if not coarser:
+                    order.append(y * width + x)
+    return order
+
+
+def progressive_preview(rgba, done: int):
+    """In-progress image after the first `done` pixels of hierarchy_order:
+    rgba [H, W, 4] holds the evaluated pixels (other entries are ignored)."""
+    rgba = np.asarray(rgba, dtype=np.float64)
+    H, W = rgba.shape[:2]
+    order = hierarchy_order(W, H)
+    evaluated = np.zeros(W * H, dtype=bool)
+    evaluated[order[:done]] = True
+    evaluated = evaluated.reshape(H, W)
+    out = np.zeros_like(rgba)
+    if done <= 0:
+        return out
+    L = hierarchy_levels(W, H)
+    lvl = L
+    for l in range(L, -1, -1):
+        nx, ny = level_dims(W, H, l)
+        if all(evaluated[b << l, a << l] for b in range(ny) for a in range(nx)):
+            lvl = l
+    nx, ny = level_dims(W, H, lvl)
+    s = float(1 << lvl)
+    for y in range(H):
+        for x in range(W):
+            if evaluated[y, x]:
+                out[y, x] = rgba[y, x]
+                continue
+            fx, fy = x / s, y / s
+            a0, b0 = min(int(np.floor(fx)), nx - 1), min(int(np.floor(fy)), ny - 1)
+            a1, b1 = min(a0 + 1, nx - 1), min(b0 + 1, ny - 1)
+            tx, ty = fx - a0, fy - b0
+            if a1 == a0:
+                tx = 0.0
+            if b1 == b0:
+                ty = 0.0
+            p00 = rgba[b0 << lvl, a0 << lvl]
+            p10 = rgba[b0 << lvl, a1 << lvl]
+            p01 = rgba[b1 << lvl, a0 << lvl]
+            p11 = rgba[b1 << lvl, a1 << lvl]
+            out[y, x] = (1 - ty) * ((1 - tx) * p00 + tx * p10) + ty * ((1 - tx) * p01 + tx * p11)
+    return out

@@ -150,3 +150,61 @@ def test_fourier_volume_recipe_matches_direct_mode_sum():
     for (k, j, i) in [(0, 0, 0), (3, 17, 8), (19, 2, 11)]:
         ref = synth.fourier_value(modes, [[ax[i], ax[j], ax[k]]])[0]
         assert abs(float(vol[k, j, i]) - (ref - lo) / (hi - lo)) < 2e-5
+
+
+# ----------------------------------------------------------------------------- progressive rendering
+def test_hierarchy_order_of_a_4x4_image_by_hand():
+    # level 2: (0,0); level 1: (2,0), (0,2), (2,2); level 0: the rest, row by row
+    assert orr.hierarchy_order(4, 4) == [0, 2, 8, 10, 1, 3, 4, 5, 6, 7, 9, 11, 12, 13, 14, 15]
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 9), (7, 5), (33, 17), (16, 16), (64, 3)])
+def test_hierarchy_order_is_a_coarse_to_fine_permutation(W, H):
+    order = orr.hierarchy_order(W, H)
+    assert sorted(order) == list(range(W * H))
+    L = orr.hierarchy_levels(W, H)
+    assert (1 << L) >= max(W, H) and (L == 0 or (1 << (L - 1)) < max(W, H))
+
+    def level(p):
+        x, y = p % W, p // W
+        l = 0
+        while l < L and x % (2 << l) == 0 and y % (2 << l) == 0:
+            l += 1
+        return l
+    lv = [level(p) for p in order]
+    assert all(a >= b for a, b in zip(lv, lv[1:]))
+    # after the pixels of levels >= l, exactly level l's grid has been evaluated
+    for l in range(L + 1):
+        nx, ny = orr.level_dims(W, H, l)
+        grid = {(b << l) * W + (a << l) for b in range(ny) for a in range(nx)}
+        assert set(order[:nx * ny]) == grid
+
+
+def test_progressive_preview_upscales_bilinear_images_exactly_and_keeps_evaluated_pixels():
+    W, H = 9, 17
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    img = np.stack([0.1 + 0.02 * x + 0.01 * y + 0.003 * x * y, 0.5 - 0.03 * y, 0.2 + 0.04 * x,
+                    0.9 - 0.001 * x * y], axis=-1)
+    # levels 5, 4 and 3 (a 2 x 3 grid) complete after 6 pixels; W-1, H-1 are multiples of 8
+    assert orr.level_dims(W, H, 3) == (2, 3)
+    np.testing.assert_allclose(orr.progressive_preview(img, 6), img, rtol=0, atol=1e-14)
+    assert np.all(orr.progressive_preview(img, 0) == 0.0)
+    noise = np.random.default_rng(3).uniform(size=img.shape)
+    full = orr.progressive_preview(noise, W * H)
+    assert np.array_equal(full, noise)
+    part = orr.progressive_preview(noise, 40)
+    done = orr.hierarchy_order(W, H)[:40]
+    flat_p, flat_n = part.reshape(-1, 4), noise.reshape(-1, 4)
+    assert np.array_equal(flat_p[done], flat_n[done])
+
+
+def test_progressive_preview_holds_the_last_coarse_column_and_row():
+    W, H = 11, 6     # level 2 grid: columns 0, 4, 8 and rows 0, 4
+    img = np.zeros((H, W, 4))
+    img[0, 0], img[0, 4], img[0, 8] = 1.0, 2.0, 3.0
+    img[4, 0], img[4, 4], img[4, 8] = 4.0, 5.0, 6.0
+    nx, ny = orr.level_dims(W, H, 2)
+    assert (nx, ny) == (3, 2)
+    pv = orr.progressive_preview(img, nx * ny)
+    assert np.allclose(pv[0, 10], 3.0) and np.allclose(pv[5, 10], 6.0) and np.allclose(pv[5, 0], 4.0)
+    assert np.allclose(pv[2, 6], 0.25 * (2 + 3 + 5 + 6))
