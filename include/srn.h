@@ -251,6 +251,24 @@ srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const 
                       float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
                       const int32_t grid[3], const int64_t* boxes, int64_t vox, float* rgba_dev);
 
+/* Progressive rendering (Sec. 6): the same pixels as srn_render, evaluated in the
+ * order of an image hierarchy.  Level l holds the pixels (a 2^l, b 2^l); the coarsest
+ * level L (the first with 2^L >= max(width, height)) is pixel (0, 0), and each finer
+ * level adds, row by row and left to right, the pixels no coarser level holds (three
+ * of every 2 x 2 block: a checkerboard).  This call renders the pixels first ..
+ * first + count - 1 of that order into rgba_dev ([height][width][4]; other pixels
+ * untouched; count is the pass's batch size: small passes answer sooner, large ones
+ * finish the frame sooner).  If preview_dev ([height][width][4], not rgba_dev) is not
+ * NULL it receives the in-progress image after first + count pixels: evaluated pixels
+ * as they are, the others the bilinear upscale of the finest complete level (sample
+ * index clamped to the level's grid; 0 when nothing is evaluated).  rgba_dev must hold
+ * the pixels of the earlier passes.  Other arguments as srn_render;
+ * width * height < 2^31, 0 <= first, 0 <= count, first + count <= width * height. */
+srn_status srn_render_progressive(srn_handle* h, void* stream, const srn_camera* cam, const float* lut_dev,
+                                  float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
+                                  const int32_t grid[3], const int64_t* boxes, int64_t vox, int64_t first,
+                                  int64_t count, float* rgba_dev, float* preview_dev);
+
 /* Checkpointing (no counterpart in the paper beyond saving trained models, Sec. 5.2).
  * The caller owns and saves the parameters, Adam moments and data ranges; these calls
  * move the rest of the training state (sampler step, Adam step counts and bias

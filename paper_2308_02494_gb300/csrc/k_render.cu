@@ -60,6 +60,34 @@ __device__ __forceinline__ Ray make_ray(const RenderParams& rp, int pix) {
   return r;
 }
 
+// Pixels of level l of the image hierarchy: its grid (a 2^l, b 2^l), ceil(W / 2^l) by
+// ceil(H / 2^l).  Together, the levels coarser than l hold exactly level l+1's grid.
+__device__ __forceinline__ int level_cols(const RenderParams& rp, int l) { return (rp.width + (1 << l) - 1) >> l; }
+__device__ __forceinline__ int level_pixels(const RenderParams& rp, int l) {
+  return level_cols(rp, l) * ((rp.height + (1 << l) - 1) >> l);
+}
+
+// Flat pixel of the k-th pixel of the render order.  Progressive order (Sec. 6): the
+// coarsest level's pixel (0, 0), then each finer level l's pixels not on level l+1's
+// grid, row by row: an even row b of the level has its odd columns, an odd row all.
+__device__ __forceinline__ int pixel_of(const RenderParams& rp, int k) {
+  if (!rp.order || k == 0) return k;
+  int l = rp.levels - 1;
+  while (level_pixels(rp, l) <= k) --l;   // level_pixels(0) = W H > k
+  const int q = k - level_pixels(rp, l + 1);
+  const int wa = level_cols(rp, l), half = wa >> 1, pair = q / (half + wa), r = q - pair * (half + wa);
+  const int a = r < half ? 2 * r + 1 : r - half, b = r < half ? 2 * pair : 2 * pair + 1;
+  return (b << l) * rp.width + (a << l);
+}
+
+// Position of pixel (x, y) in the progressive order (the inverse of pixel_of).
+__device__ __forceinline__ int order_of(const RenderParams& rp, int x, int y) {
+  if ((x | y) == 0) return 0;
+  const int l = __ffs(x | y) - 1;   // the finest level holding the pixel; < L since x, y < 2^L
+  const int a = x >> l, b = y >> l, wa = level_cols(rp, l), half = wa >> 1;
+  return level_pixels(rp, l + 1) + (b >> 1) * (half + wa) + ((b & 1) ? half + a : a >> 1);
+}
+
 // Samples of a block take their rank in their brick's bucket in three levels: lanes of
 // a warp with the same brick (match), one shared-memory count per warp group, one global
 // reservation per brick per block.  A block's samples stay together in each bucket.
@@ -77,7 +105,7 @@ __global__ void __launch_bounds__(256) k_render_gen(RenderParams rp, int pix0, i
     uint32_t b = 0xffffffffu;
     if (idx < total) {
       const int ray = (int)(idx / rp.samples), j = (int)(idx % rp.samples);
-      const Ray r = make_ray(rp, pix0 + ray);
+      const Ray r = make_ray(rp, pixel_of(rp, pix0 + ray));
       if (r.hit) {
         const float t = r.t0 + ((float)j + 0.5f) * r.dt;
         const float p[3] = {r.ox + t * r.dx, r.oy + t * r.dy, r.oz + t * r.dz};
@@ -168,7 +196,8 @@ __global__ void k_render_composite(RenderParams rp, int pix0, int npix, const ui
                                    float* __restrict__ rgba) {
   const int ray = blockIdx.x * blockDim.x + threadIdx.x;
   if (ray >= npix) return;
-  const Ray r = make_ray(rp, pix0 + ray);
+  const int pix = pixel_of(rp, pix0 + ray);
+  const Ray r = make_ray(rp, pix);
   float cr = 0.f, cg = 0.f, cb = 0.f, T = 1.f;
   if (r.hit) {
     const float k = r.dt / (2.f / 512.f);
@@ -188,7 +217,37 @@ __global__ void k_render_composite(RenderParams rp, int pix0, int npix, const ui
       T *= 1.f - alpha;
     }
   }
-  reinterpret_cast<float4*>(rgba)[pix0 + ray] = make_float4(cr, cg, cb, 1.f - T);
+  reinterpret_cast<float4*>(rgba)[pix] = make_float4(cr, cg, cb, 1.f - T);
+}
+
+// In-progress image of progressive rendering: evaluated pixels as they are, the others
+// bilinear between the four samples of the finest complete level around (x, y) / 2^l.
+__global__ void k_render_preview(RenderParams rp, int done, int level, const float4* __restrict__ rgba,
+                                 float4* __restrict__ out) {
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= rp.width * rp.height) return;
+  const int x = pix % rp.width, y = pix / rp.width;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (order_of(rp, x, y) < done) {
+    v = rgba[pix];
+  } else if (done > 0) {
+    const int nx = level_cols(rp, level), ny = (rp.height + (1 << level) - 1) >> level;
+    const float s = 1.f / (float)(1 << level);
+    const float fx = (float)x * s, fy = (float)y * s;   // exact: a power-of-two scale
+    const int a0 = min(x >> level, nx - 1), b0 = min(y >> level, ny - 1);
+    const int a1 = min(a0 + 1, nx - 1), b1 = min(b0 + 1, ny - 1);
+    const float tx = a1 == a0 ? 0.f : fx - (float)a0, ty = b1 == b0 ? 0.f : fy - (float)b0;
+    const float4 p00 = rgba[(b0 << level) * rp.width + (a0 << level)];
+    const float4 p10 = rgba[(b0 << level) * rp.width + (a1 << level)];
+    const float4 p01 = rgba[(b1 << level) * rp.width + (a0 << level)];
+    const float4 p11 = rgba[(b1 << level) * rp.width + (a1 << level)];
+    const float ux = 1.f - tx, uy = 1.f - ty;
+    v.x = uy * (ux * p00.x + tx * p10.x) + ty * (ux * p01.x + tx * p11.x);
+    v.y = uy * (ux * p00.y + tx * p10.y) + ty * (ux * p01.y + tx * p11.y);
+    v.z = uy * (ux * p00.z + tx * p10.z) + ty * (ux * p01.z + tx * p11.z);
+    v.w = uy * (ux * p00.w + tx * p10.w) + ty * (ux * p01.w + tx * p11.w);
+  }
+  out[pix] = v;
 }
 
 int blocks_for(int64_t n, int threads, int num_sms) {
@@ -221,6 +280,14 @@ cudaError_t launch_render_batch(const Launch& L, const RenderParams& rp, const R
              : launch_query_fp32(L, kForward, md, gr, br, tw, w.xyz, nullptr, w.val);
   if (e != cudaSuccess) return e;
   k_render_composite<<<(npix + 127) / 128, 128, 0, L.stream>>>(rp, pix0, npix, w.pos, w.val, lut, rgba);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_preview(const Launch& L, const RenderParams& rp, int done, int level,
+                                  const float* rgba, float* preview) {
+  const int n = rp.width * rp.height;
+  k_render_preview<<<(n + 255) / 256, 256, 0, L.stream>>>(rp, done, level, reinterpret_cast<const float4*>(rgba),
+                                                         reinterpret_cast<float4*>(preview));
   return cudaGetLastError();
 }
 

@@ -8,6 +8,8 @@ namespace srn {
 struct RenderParams {
   srn_camera cam;
   int32_t width, height, samples;
+  int32_t order;    // 0: raster order; 1: the progressive (image-hierarchy) order
+  int32_t levels;   // L: the coarsest hierarchy level, 2^L >= max(width, height)
   int32_t grid[3];
   int64_t vox;
   float vmin, vmax;
@@ -28,6 +30,10 @@ struct RenderWs {
 
 cudaError_t launch_render_batch(const Launch& L, const RenderParams& rp, const RenderWs& w, int pix0,
                                 int npix, const Model& md, const float* lut, float* rgba);
+// In-progress image after `done` pixels of the progressive order; `level` is the finest
+// complete hierarchy level (ignored when done = 0).
+cudaError_t launch_render_preview(const Launch& L, const RenderParams& rp, int done, int level,
+                                  const float* rgba, float* preview);
 
 // One batch of the full-volume decode: the voxels [x0, x0+nx) x [y0, y0+ny) x [z0, z0+nz)
 // (all in brick `brick`, x fastest) queried in that brick's local coordinates.

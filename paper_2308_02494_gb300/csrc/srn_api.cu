@@ -827,22 +827,31 @@ srn_status srn_decode(srn_handle* h, void* stream, const int32_t grid[3], const 
   return SRN_OK;
 }
 
-srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const float* lut,
-                      float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
-                      const int32_t grid[3], const int64_t* boxes, int64_t vox, float* rgba) {
+}  // extern "C"
+
+namespace {
+
+// Checks the arguments shared by the render entry points and fills rp.
+srn_status render_params(srn_handle* h, const srn_camera* cam, const float* lut, float vmin, float vmax,
+                         int32_t width, int32_t height, int32_t samples, const int32_t grid[3],
+                         const int64_t* boxes, int64_t vox, float* rgba, srn::RenderParams& rp) {
   srn_status s = check_handle(h);
   if (s != SRN_OK) return s;
   if (!cam || !lut || !grid || !boxes || !rgba) return fail(SRN_ERR_INVALID_ARG, "NULL argument");
   if (width < 1 || height < 1 || samples < 1) return fail(SRN_ERR_INVALID_ARG, "empty image or no samples");
+  if ((int64_t)width * height > INT32_MAX) return fail(SRN_ERR_INVALID_ARG, "image of 2^31 pixels or more");
   if ((int64_t)samples > h->max_points)
     return fail(SRN_ERR_INVALID_ARG, "samples per ray %d exceed max_points", samples);
   if (!(vmax > vmin)) return fail(SRN_ERR_INVALID_ARG, "vmax must exceed vmin");
   if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1 || grid[0] * grid[1] * grid[2] != h->cfg.n_bricks)
     return fail(SRN_ERR_INVALID_ARG, "brick grid does not match n_bricks");
   if (vox < 2) return fail(SRN_ERR_INVALID_ARG, "vox < 2");
-  srn::RenderParams rp{};
+  rp = srn::RenderParams{};
   rp.cam = *cam;
   rp.width = width; rp.height = height; rp.samples = samples;
+  rp.order = 0;
+  rp.levels = 0;
+  while ((1 << rp.levels) < std::max(width, height)) ++rp.levels;
   for (int a = 0; a < 3; ++a) rp.grid[a] = grid[a];
   rp.vox = vox; rp.vmin = vmin; rp.vmax = vmax;
   for (int b = 0; b < h->cfg.n_bricks; ++b)
@@ -851,6 +860,13 @@ srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const 
       if (lo < 0 || hi >= vox || hi <= lo) return fail(SRN_ERR_INVALID_ARG, "box of brick %d invalid", b);
       rp.lo[b][a] = (int32_t)lo; rp.hi[b][a] = (int32_t)hi;
     }
+  return SRN_OK;
+}
+
+// Renders the pixels first .. first + count - 1 of rp's order in batches of at most
+// max_points samples.
+srn_status render_pixels(srn_handle* h, void* stream, const srn::RenderParams& rp, const float* lut,
+                         int64_t first, int64_t count, float* rgba) {
   unsigned char* ws = h->ws;
   srn::RenderWs w;
   w.loc = reinterpret_cast<float*>(ws + h->wl.r_loc);
@@ -861,13 +877,53 @@ srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const 
   w.val = reinterpret_cast<float*>(ws + h->wl.r_val);
   w.cnt = reinterpret_cast<uint32_t*>(ws + h->wl.r_cnt);
   w.off = reinterpret_cast<int64_t*>(ws + h->wl.r_off);
-  const int64_t npix = (int64_t)width * height;
-  const int64_t batch = h->max_points / samples;
+  const int64_t batch = h->max_points / rp.samples;
   const srn::Model md = h->model();
-  for (int64_t p0 = 0; p0 < npix; p0 += batch) {
-    const int n = (int)std::min<int64_t>(batch, npix - p0);
+  for (int64_t p0 = first; p0 < first + count; p0 += batch) {
+    const int n = (int)std::min<int64_t>(batch, first + count - p0);
     cudaError_t e = srn::launch_render_batch(h->launch(stream), rp, w, (int)p0, n, md, lut, rgba);
     if (e != cudaSuccess) return cuda_fail(e, "render");
+  }
+  return SRN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+srn_status srn_render(srn_handle* h, void* stream, const srn_camera* cam, const float* lut,
+                      float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
+                      const int32_t grid[3], const int64_t* boxes, int64_t vox, float* rgba) {
+  srn::RenderParams rp;
+  srn_status s = render_params(h, cam, lut, vmin, vmax, width, height, samples, grid, boxes, vox, rgba, rp);
+  if (s != SRN_OK) return s;
+  return render_pixels(h, stream, rp, lut, 0, (int64_t)width * height, rgba);
+}
+
+srn_status srn_render_progressive(srn_handle* h, void* stream, const srn_camera* cam, const float* lut,
+                                  float vmin, float vmax, int32_t width, int32_t height, int32_t samples,
+                                  const int32_t grid[3], const int64_t* boxes, int64_t vox, int64_t first,
+                                  int64_t count, float* rgba, float* preview) {
+  srn::RenderParams rp;
+  srn_status s = render_params(h, cam, lut, vmin, vmax, width, height, samples, grid, boxes, vox, rgba, rp);
+  if (s != SRN_OK) return s;
+  const int64_t npix = (int64_t)width * height;
+  if (first < 0 || count < 0 || first + count > npix)
+    return fail(SRN_ERR_INVALID_ARG, "pixels [%lld, %lld) outside the image of %lld", (long long)first,
+                (long long)(first + count), (long long)npix);
+  if (preview == rgba) return fail(SRN_ERR_INVALID_ARG, "preview_dev must not be rgba_dev");
+  rp.order = 1;
+  if ((s = render_pixels(h, stream, rp, lut, first, count, rgba)) != SRN_OK) return s;
+  if (preview) {
+    const int64_t done = first + count;
+    int level = rp.levels;   // the finest level whose whole grid is among the first `done` pixels
+    while (level > 0) {
+      const int64_t nx = (width + (1 << (level - 1)) - 1) >> (level - 1), ny = (height + (1 << (level - 1)) - 1) >> (level - 1);
+      if (nx * ny > done) break;
+      --level;
+    }
+    cudaError_t e = srn::launch_render_preview(h->launch(stream), rp, (int)done, level, rgba, preview);
+    if (e != cudaSuccess) return cuda_fail(e, "render preview");
   }
   return SRN_OK;
 }

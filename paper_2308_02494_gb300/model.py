@@ -166,6 +166,18 @@ class SRN:
                       samples, grid, np.asarray(boxes).ravel(), vox, rgba.data_ptr())
         return rgba
 
+    def render_progressive(self, cam: dict, lut: torch.Tensor, vmin, vmax, width, height, samples, grid, boxes,
+                           vox, first, count, rgba, preview=None, stream=None):
+        """One pass of progressive rendering (srn_render_progressive): pixels first ..
+        first + count - 1 of the image-hierarchy order into rgba, and, if preview is
+        given, the in-progress image after them."""
+        c = _s.Camera((ct_f3(cam["eye"])), ct_f3(cam["forward"]), ct_f3(cam["right"]), ct_f3(cam["up"]),
+                      float(cam["scale"]), 1 if cam["ortho"] else 0)
+        _s.srn_render_progressive(self.handle, _stream_ptr(stream), c, lut.data_ptr(), vmin, vmax, width, height,
+                                  samples, grid, np.asarray(boxes).ravel(), vox, first, count, rgba.data_ptr(),
+                                  preview.data_ptr() if preview is not None else None)
+        return rgba
+
     # ------------------------------------------------------------------ checkpoints
     def save(self, path, stream=None) -> None:
         """Write a checkpoint: parameters, Adam moments, data ranges and the library's

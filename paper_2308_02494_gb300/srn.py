@@ -35,7 +35,7 @@ EXPORTS = (
     "srn_sync_shadow", "srn_sample_points", "srn_sample_target", "srn_forward", "srn_backward",
     "srn_step", "srn_train_step", "srn_render", "srn_set_timing", "srn_read_timing", "srn_get_status",
     "srn_sample_points_static", "srn_decode", "srn_state_bytes", "srn_save_state", "srn_load_state",
-    "srn_set_schedule", "srn_read_schedule",
+    "srn_set_schedule", "srn_read_schedule", "srn_render_progressive",
 )
 SRN_STATIC_SAMPLER_MAX_POINTS = 131072
 SRN_STATIC_SAMPLER_MAX_BRICKS = 8
@@ -109,6 +109,8 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
         "srn_step": [P, P, U32],
         "srn_train_step": [P, P, U64, P, I64P, I64P, I64P, U32, P, P, P],
         "srn_render": [P, P, ct.POINTER(Camera), P, F, F, I32, I32, I32, ct.POINTER(I32), I64P, I64, P],
+        "srn_render_progressive": [P, P, ct.POINTER(Camera), P, F, F, I32, I32, I32, ct.POINTER(I32), I64P, I64,
+                                   I64, I64, P, P],
         "srn_get_status": [P, P],
         "srn_set_timing": [P, I32],
         "srn_read_timing": [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)],
@@ -200,6 +202,13 @@ def srn_render(h, stream, cam: Camera, lut, vmin, vmax, width, height, samples, 
     g = (ct.c_int32 * 3)(*[int(v) for v in grid])
     _check(load().srn_render(h, stream, ct.byref(cam), lut, vmin, vmax, width, height, samples, g,
                              _i64(boxes), vox, rgba))
+
+
+def srn_render_progressive(h, stream, cam: Camera, lut, vmin, vmax, width, height, samples, grid, boxes, vox,
+                           first, count, rgba, preview) -> None:
+    g = (ct.c_int32 * 3)(*[int(v) for v in grid])
+    _check(load().srn_render_progressive(h, stream, ct.byref(cam), lut, vmin, vmax, width, height, samples, g,
+                                         _i64(boxes), vox, int(first), int(count), rgba, preview))
 
 
 SRN_TIME_OFF, SRN_TIME_QUERY, SRN_TIME_ENCODER, SRN_TIME_DECODER, SRN_TIME_SCATTER = range(5)

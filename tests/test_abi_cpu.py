@@ -15,8 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def lib():
-    if not os.path.exists(pb.LIB):
-        pb.build()
+    pb.build()   # incremental: recompiles only sources newer than their objects
     return srn.load()
 
 
