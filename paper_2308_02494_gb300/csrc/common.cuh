@@ -66,7 +66,7 @@ struct TrainWs {
   int32_t* status;  // device status word
   int32_t upstream; // 1: the target slot holds dL/df (no L_rec); 0: MSE against targets
   __nv_bfloat16* Y;   // [N][K] features (BF16 training pass)
-  __nv_bfloat16* dY;  // [M][N][C] dL/dy, grid-major (BF16 training pass)
+  __nv_bfloat16* dY;  // [N][M][C] dL/dy, point-major like Y (BF16 training pass)
   int32_t* ustart;    // [B][kUnits + 1] first point of each Morton unit (BF16 scatter tiles)
   struct ScatTile* tiles;  // scatter tiles (BF16 training pass)
   int32_t* tile_ctr;  // [0] tiles written, [1] next tile to take

@@ -81,7 +81,6 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
   const int total = tm.first[br.n];
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int tb = blockIdx.x * per, te = min(total, tb + per);
-  const int64_t ntot = br.off[br.n];
   const int r = tid;   // the tile row this thread owns in the epilogues
 
   uint32_t phase = 0;
@@ -315,20 +314,19 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     }
     wait_mma();
     if (tile + 1 < te && !gave_up) prefetch(tile + 1);   // Y has been read by every MMA of this tile
-    // ---- dL/dy to global memory, grid-major bf16: dY[i][p][c] (column 2i + c)
+    // ---- dL/dy to global memory, point-major bf16: row p0 + r holds the K features'
+    //      gradients in feature order (grid-major, channel-minor, as Y)
 #pragma unroll
     for (int c0 = 0; c0 < TK; c0 += 16) {
-      uint32_t z[16];
+      uint32_t z[16], d[8];
       tc::ld16(trow + kColDY + c0, z);
       tc::ld_wait();
-      if (rv && md.C == 2) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-          reinterpret_cast<uint32_t*>(ws.dY)[(int64_t)(c0 / 2 + i) * ntot + p0 + r] =
-              pack_bf16(bits(z[2 * i]), bits(z[2 * i + 1]));
-      } else if (rv) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) ws.dY[(int64_t)(c0 + i) * ntot + p0 + r] = __float2bfloat16_rn(bits(z[i]));
+      for (int i = 0; i < 8; ++i) d[i] = pack_bf16(bits(z[2 * i]), bits(z[2 * i + 1]));
+      if (rv) {
+        uint4* o = reinterpret_cast<uint4*>(ws.dY + (p0 + r) * TK + c0);
+        o[0] = make_uint4(d[0], d[1], d[2], d[3]);
+        o[1] = make_uint4(d[4], d[5], d[6], d[7]);
       }
     }
     fresh = false;

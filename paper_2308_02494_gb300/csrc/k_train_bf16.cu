@@ -6,21 +6,19 @@
 //  k_mlp   decoder forward and backward for K < 128 on the tensor cores (mma.sync
 //          m16n8k16, BF16 operands, FP32 accumulation): L_rec partial sums,
 //          h(x) = (f - v)^2, dW1/dW2/dw3 accumulated in registers per CTA and flushed
-//          once, and dL/dy written grid-major as bf16 (dY [M][N][C]) for the scatter.
+//          once, and dL/dy written point-major as bf16 (dY [N][M][C], like Y).
 //          K = 128 runs on tcgen05 instead (k_mlp_tc.cu).
 //  k_scat  adjoint of Eq. 2.  A tile is up to 1024 points of one brick lying in one
 //          aligned Morton range of the sampler's bins (a small axis-aligned block of
-//          the brick), listed by k_unit_starts / k_tile_list.  The CTA takes the grids
-//          one at a time: the tile's block, mapped through the grid's Eq. 1, bounds
-//          the node box; the CTA counting-sorts the tile's points by their cell in that
-//          box (integer shared-memory atomics, a block-wide scan), sums each cell's
-//          eight corner contributions with plain FMAs into corner-major per-cell sums,
-//          and lets every node of the box gather its (up to) eight cells and add the
-//          total into the float32 gradient grid with one float2 atomic.  When the box
-//          exceeds the shared-memory capacity the tile falls back to the exact box of
-//          its points, of each half, of each 256-point chunk, then to adding each
-//          point's corners directly; so do single points outside their tile's block
-//          (a batch that is not Morton-sorted is correct, only slower).
+//          the brick), listed by k_unit_starts / k_tile_list.  Lane l of a warp takes
+//          grid l (of a group of 32): the block, mapped through the grid's Eq. 1,
+//          bounds a node box that the tile's level keeps within shared memory, and the
+//          warp adds one point's eight corners into 32 grids' boxes at once, as 32-bit
+//          fixed-point integers (a power-of-two scale per grid and tile from its
+//          largest |dL/dy|) with shared-memory integer reductions, one bank per lane.
+//          Each box node then goes into the float32 gradient grid with one atomic.
+//          Points outside their tile's box (rounding at its faces; a batch that is not
+//          Morton-sorted) add their corners directly.
 #include "bf16_ops.cuh"
 #include "kernels.h"
 #include <algorithm>
@@ -165,7 +163,6 @@ k_mlp(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ targ
   const int total = tm.first[br.n];
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int tb = blockIdx.x * per, te = min(total, tb + per);
-  const int64_t ntot = br.off[br.n];
   float* w3s = reinterpret_cast<float*>(sm + L::W3);
   float* vs = reinterpret_cast<float*>(sm + L::V);
   float* dys = reinterpret_cast<float*>(sm + L::DY);
@@ -429,11 +426,11 @@ k_mlp(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ targ
         }
       }
     }
-    // ---- dL/dy to global memory, grid-major bf16: dY[i][p][c]
+    // ---- dL/dy to global memory, point-major bf16: dY[p][i][c]
     for (int idx = tid; idx < M * T; idx += NT) {
-      const int i = idx / T, p = idx % T;
+      const int p = idx / M, i = idx % M;
       if (p < np) {
-        const int64_t o = (int64_t)i * ntot + p0 + p;
+        const int64_t o = (p0 + p) * M + i;
         if (C == 2) {
           const float2 g = *reinterpret_cast<const float2*>(dys + p * L::DYS + 2 * i);
           reinterpret_cast<uint32_t*>(ws.dY)[o] = pack_bf16(g.x, g.y);
@@ -448,320 +445,83 @@ k_mlp(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ targ
 }
 
 // =============================================================================== k_scat
-constexpr int ST = 1024;        // Morton-consecutive points per scatter tile
-constexpr int SNT = 256;
-constexpr int PPT = ST / SNT;   // points per thread (point tid + 256 j belongs to chunk j)
-constexpr int CCAP = 512;       // cells of a usable box
-constexpr int NCAP = 1024;      // nodes of a usable box
+constexpr int ST = 1024;        // Morton-consecutive points per scatter tile (at most)
+constexpr int SNT = 512;        // threads of k_scat (one CTA per SM)
+constexpr int SNW = SNT / 32;
+constexpr int kTileLevelCap = 9;            // largest Morton level of a scatter tile
+constexpr float kMagic = 12582912.f;        // 1.5 * 2^23: for |x| < 2^22, x + kMagic holds round(x)
+constexpr int32_t kMagicBits = 0x4B400000;  // in its low bits, offset by these bits of kMagic
 
-// Shared memory of k_scat (dynamic): per-point data, the counting sort, per-cell
-// corner sums (corner-major, conflict-free) and the carried partial sums.
-struct ScatSmem {
-  float cs[16 * CCAP];         // per-cell corner sums: corner k, cell l, channel e at (k CCAP + l) C + e
-  float pl[16 * SNT];          // chunk t's last partial sums (its cell goes on past the chunk): (k SNT + t) C + e
-  uint2 tbox[kMaxGrids];       // the tile's node box in every grid (lo and node counts, bytes)
-  float4 wg[ST];               // per point: grid coordinates s (Eq. 2), then, for the points of a
-                               // box pass, the cell weights; .w holds dL/dy (bf16 x 2 bits)
-  int cnt[CCAP + 1];           // cell counts, then starts; all zero between passes
-  alignas(16) unsigned short perm[ST];    // point indices ordered by cell
-  alignas(16) unsigned short pcell[ST];    // the cell of each sorted position
-  int red[2][SNT / 32][6];     // block min/max scratch (alternating between calls)
-  int wsum[SNT / 32];          // block scan scratch
+// Head of k_scat's dynamic shared memory; the tile's fixed-point node boxes follow it,
+// [group][node][channel][32 columns] int32 (see ScatMap).
+struct ScatHead {
+  float4 xs[ST];               // the tile's points
+  uint2 box[kMaxGrids];        // node box of the tile's block per grid: lo | nodes per axis (bytes)
+  uint32_t gmax[kMaxGrids];    // largest |dL/dy| of the tile per grid (bf16 bits)
+  ScatTile tile;
 };
 
-struct Box {
-  int lo[3], n[3];   // first node and nodes per axis of the box
-  int ncells;
-  bool ok;
+// Thread -> grid, column group and point group of k_scat.  With M >= 32 the lanes of a
+// warp take 32 consecutive grids (group w mod M/32) and the warps of a group split the
+// tile's points; with M < 32 lane l takes grid l mod M and a warp 32/M points at a time.
+// A grid group's boxes are stored node by node with one column per lane, so the 32
+// reductions of a warp instruction always fall in 32 different banks.
+struct ScatMap {
+  int g, grp, pg, npg;
 };
-
-// Exact node box of the cells in [mn, mx] (per axis, cell coordinates), reduced over
-// the block; empty when no point was inside the grid.  Consecutive calls alternate
-// between two scratch rows (`parity`), so one barrier per call suffices: a row is
-// rewritten only after every thread has passed the barrier of the call in between.
-__device__ __forceinline__ Box block_box(ScatSmem& s, int (&mn)[3], int (&mx)[3], unsigned& parity) {
+__device__ __forceinline__ ScatMap scat_map(int M) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int (*red)[6] = s.red[parity & 1u];
-  ++parity;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    mn[d] = __reduce_min_sync(0xffffffffu, mn[d]);
-    mx[d] = __reduce_max_sync(0xffffffffu, mx[d]);
-  }
-  if (lane == 0)
-    for (int d = 0; d < 3; ++d) { red[warp][d] = mn[d]; red[warp][3 + d] = mx[d]; }
-  __syncthreads();
-  Box bx;
-  for (int d = 0; d < 3; ++d) {
-    int lo = red[0][d], hi = red[0][3 + d];
-    for (int q = 1; q < SNT / 32; ++q) { lo = min(lo, red[q][d]); hi = max(hi, red[q][3 + d]); }
-    bx.lo[d] = lo;
-    bx.n[d] = hi >= lo ? hi - lo + 2 : 0;
-  }
-  bx.ncells = bx.n[0] ? (bx.n[0] - 1) * (bx.n[1] - 1) * (bx.n[2] - 1) : 0;
-  bx.ok = bx.ncells > 0 && bx.ncells <= CCAP && bx.n[0] * bx.n[1] * bx.n[2] <= NCAP;
-  return bx;
-}
-
-// Adds the eight corner weights of one point (wg entry v) times its dL/dy into a.
-template <int C>
-__device__ __forceinline__ void add_corners(float (&a)[8][C], const float4 v) {
-  const float wx = v.x, wy = v.y, wz = v.z, ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
-  const float zy[4] = {az * ay, az * wy, wz * ay, wz * wy};
-  const float2 g = unpack_bf16(__float_as_uint(v.w));
-  const float ge[2] = {g.x, g.y};
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const float wt = zy[k >> 1] * ((k & 1) ? wx : ax);
-#pragma unroll
-    for (int e = 0; e < C; ++e) a[k][e] = fmaf(wt, ge[e], a[k][e]);
-  }
-}
-
-// Counting sort of the points with id >= 0 by cell (each already holds its rank rk
-// among its cell's points, taken with an atomic on s.cnt), per-cell corner sums, node
-// gather and one atomic per nonzero node of the box.  Leaves s.cnt zero.  The corner sums are balanced over threads: thread t sums the sorted
-// positions 4t..4t+3 run by run.  A run that is a whole cell is stored as the cell's
-// sum; the chunk's last run, when its cell goes on into the next chunk, is parked in
-// pl[.][t]; the chunk's first run, when its cell began in an earlier chunk, is that
-// cell's last piece, and this thread adds the parked pieces of the cell's earlier
-// chunks to it and stores the sum.
-// Corner k's C sums of cell l (a float2 when C = 2) in the layouts of ScatSmem.
-template <int C>
-__device__ __forceinline__ void put_sums(float* base, int k, int l, int cap, const float (&a)[8][C]) {
-  if (C == 2) *reinterpret_cast<float2*>(base + ((k * cap + l) << 1)) = make_float2(a[k][0], a[k][C - 1]);
-  else base[k * cap + l] = a[k][0];
-}
-template <int C>
-__device__ __forceinline__ void add_sums(const float* base, int k, int l, int cap, float (&a)[8][C]) {
-  if (C == 2) {
-    const float2 v = *reinterpret_cast<const float2*>(base + ((k * cap + l) << 1));
-    a[k][0] += v.x;
-    a[k][C - 1] += v.y;
+  ScatMap m;
+  if (M >= 32) {
+    const int ngrp = M >> 5;
+    m.grp = warp % ngrp;
+    m.g = m.grp * 32 + lane;
+    m.pg = warp / ngrp;
+    m.npg = SNW / ngrp;
   } else {
-    a[k][0] += base[k * cap + l];
+    m.grp = 0;
+    m.g = lane % M;
+    m.pg = warp * (32 / M) + lane / M;
+    m.npg = SNW * (32 / M);
   }
+  return m;
 }
 
+// Power-of-two scale of one grid's fixed-point sums over a tile of np points whose
+// largest |dL/dy| has bf16 bits mb: every product w g scale stays below 2^B <= 2^22 in
+// magnitude (so kMagic rounds it exactly) and every node's sum below np 2^B <= 2^30
+// (each point adds at most |g| to a node).  inv = 1 / scale exactly.
+__device__ __forceinline__ float fixed_scale(uint32_t mb, int np, float& inv) {
+  const int lognp = 32 - __clz(max(np - 1, 1));   // ceil(log2 np)
+  const int B = min(22, 30 - lognp);
+  const int ef = (int)((mb >> 7) & 0xffu);          // biased exponent: max|g| < 2^(ef - 126)
+  const int sb = min(B + 253 - ef, 250);            // scale = 2^(sb - 127) <= 2^(B + 126 - ef)
+  inv = __int_as_float((254 - sb) << 23);
+  return __int_as_float(sb << 23);
+}
+__device__ __forceinline__ int32_t fixed_pt(float w, float gs) {
+  return __float_as_int(fmaf(w, gs, kMagic)) - kMagicBits;
+}
+template <int OFF>
+__device__ __forceinline__ void red_s32(uint32_t a, int32_t v) {
+  asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(a), "r"(v), "n"(OFF));
+}
+// The two x-neighbour corners (weights wa at x, wb at x + 1) of one (y, z) corner pair.
 template <int C>
-__device__ void box_pass(ScatSmem& s, const Box& bx, float* dFi, int R, const short (&id)[PPT],
-                         const int (&rk)[PPT]) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ncx = bx.n[0] - 1, ncy = bx.n[1] - 1, ncz = bx.n[2] - 1, ncells = bx.ncells;
-  {  // cells without points must read as zero in the gather
-    const int n4 = (ncells * C + 3) >> 2;   // float4 per corner row
-    for (int l = tid; l < n4; l += SNT)
-#pragma unroll
-      for (int k = 0; k < 8; ++k) reinterpret_cast<float4*>(s.cs + k * CCAP * C)[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+__device__ __forceinline__ void red_pair(uint32_t a, float wa, float wb, float gs0, float gs1) {
+  red_s32<0>(a, fixed_pt(wa, gs0));
+  red_s32<C * 128>(a, fixed_pt(wb, gs0));
+  if constexpr (C == 2) {
+    red_s32<128>(a, fixed_pt(wa, gs1));
+    red_s32<C * 128 + 128>(a, fixed_pt(wb, gs1));
   }
-  __syncthreads();   // the callers took every point's rank in its cell (s.cnt) before
-  {  // block-wide exclusive scan, two consecutive cells per thread
-    const int l0 = 2 * tid;
-    const int c0 = l0 < ncells ? s.cnt[l0] : 0, c1 = l0 + 1 < ncells ? s.cnt[l0 + 1] : 0;
-    const int run = c0 + c1;
-    int incl = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    if (lane == 31) s.wsum[warp] = incl;
-    __syncthreads();
-    int base = 0;
-    for (int q = 0; q < warp; ++q) base += s.wsum[q];
-    const int ex = base + incl - run;
-    if (l0 < ncells) s.cnt[l0] = ex;
-    if (l0 + 1 < ncells) s.cnt[l0 + 1] = ex + c0;
-    if (tid == SNT - 1) s.cnt[ncells] = base + incl;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < PPT; ++j)
-    if (rk[j] >= 0) {
-      const int pos = s.cnt[id[j]] + rk[j];
-      s.perm[pos] = (unsigned short)(tid + SNT * j);
-      s.pcell[pos] = (unsigned short)id[j];
-    }
-  __syncthreads();
-  const int n_act = s.cnt[ncells];
-  const int q0 = 4 * tid;
-  int head_cell = -1, head_from = 0;   // the chunk's first run, when its cell began in an earlier chunk
-  if (q0 < n_act) {
-    const int nq = min(4, n_act - q0);
-    const uint2 pp = *reinterpret_cast<const uint2*>(s.perm + q0);
-    const uint2 pc = *reinterpret_cast<const uint2*>(s.pcell + q0);
-    const int idx[4] = {(int)(pp.x & 0xffffu), (int)(pp.x >> 16), (int)(pp.y & 0xffffu), (int)(pp.y >> 16)};
-    const int cel[4] = {(int)(pc.x & 0xffffu), (int)(pc.x >> 16), (int)(pc.y & 0xffffu), (int)(pc.y >> 16)};
-    float4 v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = u < nq ? s.wg[idx[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int start0 = s.cnt[cel[0]];
-    float a[8][C];
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-#pragma unroll
-      for (int e = 0; e < C; ++e) a[k][e] = 0.f;
-    int cur = cel[0];
-    bool first = true;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (u < nq) {
-        if (u > 0 && cel[u] != cur) {   // cell cur ended inside the chunk
-          if (first && start0 < q0) head_cell = cur;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) put_sums<C>(s.cs, k, cur, CCAP, a);
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int e = 0; e < C; ++e) a[k][e] = 0.f;
-          cur = cel[u];
-          first = false;
-        }
-        add_corners<C>(a, v[u]);
-      }
-    }
-    if (s.cnt[cur + 1] > q0 + 4) {   // the last run goes on into the next chunk
-#pragma unroll
-      for (int k = 0; k < 8; ++k) put_sums<C>(s.pl, k, tid, SNT, a);
-    } else {
-      if (first && start0 < q0) head_cell = cur;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) put_sums<C>(s.cs, k, cur, CCAP, a);
-    }
-    head_from = start0 >> 2;
-  }
-  __syncthreads();
-  if (head_cell >= 0) {   // last piece of a cell spanning chunks head_from .. tid
-    float acc[8][C], acc2[8][C];   // two chunks per iteration: independent loads in flight
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-#pragma unroll
-      for (int e = 0; e < C; ++e) { acc[k][e] = 0.f; acc2[k][e] = 0.f; }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) add_sums<C>(s.cs, k, head_cell, CCAP, acc);
-    int j = head_from;
-    for (; j + 1 < tid; j += 2)
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        add_sums<C>(s.pl, k, j, SNT, acc);
-        add_sums<C>(s.pl, k, j + 1, SNT, acc2);
-      }
-    if (j < tid)
-#pragma unroll
-      for (int k = 0; k < 8; ++k) add_sums<C>(s.pl, k, j, SNT, acc);
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-#pragma unroll
-      for (int e = 0; e < C; ++e) acc[k][e] += acc2[k][e];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) put_sums<C>(s.cs, k, head_cell, CCAP, acc);
-  }
-  __syncthreads();
-  for (int l = tid; l <= ncells; l += SNT) s.cnt[l] = 0;   // ready for the next pass
-  const int nodes = bx.n[0] * bx.n[1] * bx.n[2];
-  const float inv_x = 1.f / (float)bx.n[0], inv_xy = 1.f / (float)(bx.n[0] * bx.n[1]);
-  const int sy = ncx, sz = ncx * ncy;   // cell index strides
-  for (int q = tid; q < nodes; q += SNT) {
-    const int qz = (int)(((float)q + 0.5f) * inv_xy);
-    const int rxy = q - qz * bx.n[0] * bx.n[1];
-    const int qy = (int)(((float)rxy + 0.5f) * inv_x);
-    const int qx = rxy - qy * bx.n[0];
-    // node (qx, qy, qz) is corner k = (dx, dy, dz) of cell (qx - dx, qy - dy, qz - dz)
-    const int l0 = (qz * ncy + qy) * ncx + qx;
-    const bool x0 = qx < ncx, x1 = qx > 0, y0 = qy < ncy, y1 = qy > 0, z0 = qz < ncz, z1 = qz > 0;
-    float v[C];
-#pragma unroll
-    for (int e = 0; e < C; ++e) v[e] = 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const bool in = ((k & 1) ? x1 : x0) && ((k & 2) ? y1 : y0) && ((k & 4) ? z1 : z0);
-      if (in) {
-        const int l = l0 - ((k & 1) ? 1 : 0) - ((k & 2) ? sy : 0) - ((k & 4) ? sz : 0);
-        if (C == 2) {
-          const float2 w = *reinterpret_cast<const float2*>(s.cs + ((k * CCAP + l) << 1));
-          v[0] += w.x;
-          v[C - 1] += w.y;
-        } else {
-          v[0] += s.cs[k * CCAP + l];
-        }
-      }
-    }
-    const int64_t g = ((int64_t)(bx.lo[2] + qz) * R + (bx.lo[1] + qy)) * R + bx.lo[0] + qx;
-    if (C == 2) {
-      if (v[0] != 0.f || v[C - 1] != 0.f)
-        atomicAdd(reinterpret_cast<float2*>(dFi) + g, make_float2(v[0], v[C - 1]));
-    } else {
-      if (v[0] != 0.f) atomicAdd(dFi + g, v[0]);
-    }
-  }
-  __syncthreads();
 }
 
-// Cell of a point from its grid coordinates (the clamped s of Eq. 2).
-__device__ __forceinline__ void cell_of(const float4 w, int R, int& cx, int& cy, int& cz) {
-  cx = min((int)w.x, R - 2);
-  cy = min((int)w.y, R - 2);
-  cz = min((int)w.z, R - 2);
-}
-
-// Box pass over this thread's points whose chunk j is in the mask jm (bit j), read from
-// s.wg.  Returns false, having changed nothing, when their box does not fit in shared
-// memory; otherwise replaces their grid coordinates in s.wg by cell weights and runs
-// the pass.
+// dL/dy of point p (global index) for grid g: C bf16 values in the low bits.
 template <int C>
-__device__ bool masked_pass(ScatSmem& s, unsigned jm, float* dFi, int R, unsigned& parity) {
-  int mn[3] = {1 << 20, 1 << 20, 1 << 20}, mx[3] = {-1, -1, -1};
-#pragma unroll
-  for (int j = 0; j < PPT; ++j)
-    if ((jm >> j) & 1u) {
-      const float4 w = s.wg[threadIdx.x + SNT * j];
-      if (__float_as_uint(w.w) & 0x7fff7fffu) {
-        int cx, cy, cz;
-        cell_of(w, R, cx, cy, cz);
-        mn[0] = min(mn[0], cx); mn[1] = min(mn[1], cy); mn[2] = min(mn[2], cz);
-        mx[0] = max(mx[0], cx); mx[1] = max(mx[1], cy); mx[2] = max(mx[2], cz);
-      }
-    }
-  const Box bx = block_box(s, mn, mx, parity);   // block-uniform
-  if (bx.n[0] == 0) return true;
-  if (!bx.ok) return false;
-  short id[PPT];
-  int rk[PPT];
-#pragma unroll
-  for (int j = 0; j < PPT; ++j) {
-    id[j] = -1;
-    rk[j] = -1;
-    if ((jm >> j) & 1u) {
-      const int p = threadIdx.x + SNT * j;
-      const float4 w = s.wg[p];
-      if (__float_as_uint(w.w) & 0x7fff7fffu) {
-        int cx, cy, cz;
-        cell_of(w, R, cx, cy, cz);
-        id[j] = (short)(((cz - bx.lo[2]) * (bx.n[1] - 1) + (cy - bx.lo[1])) * (bx.n[0] - 1) + (cx - bx.lo[0]));
-        s.wg[p] = make_float4(w.x - (float)cx, w.y - (float)cy, w.z - (float)cz, w.w);
-        rk[j] = atomicAdd(s.cnt + id[j], 1);
-      }
-    }
-  }
-  box_pass<C>(s, bx, dFi, R, id, rk);
-  return true;
-}
-
-// Largest Morton level (a range of 2^L units) whose block keeps the node box of a
-// grid with R nodes per axis, mapped without distortion, within 80% of the capacities.
-int scat_lmax(int R) {
-  const double cells_per_unit = (double)(R - 1) / (double)(1 << kUnitBits);
-  for (int L = 5; L > 0; --L) {
-    const int ext[3] = {1 << ((L + 2) / 3), 1 << ((L + 1) / 3), 1 << (L / 3)};
-    int64_t cells = 1, nodes = 1;
-    for (int d = 0; d < 3; ++d) {
-      const int c = (int)std::ceil(ext[d] * cells_per_unit) + 1;
-      cells *= c;
-      nodes *= c + 1;
-    }
-    if (cells <= CCAP * 4 / 5 && nodes <= NCAP * 4 / 5) return L;
-  }
-  return 0;
+__device__ __forceinline__ uint32_t dy_bits(const __nv_bfloat16* dY, int64_t p, int M, int g) {
+  if constexpr (C == 2) return __ldg(reinterpret_cast<const unsigned int*>(dY) + p * M + g);
+  else return (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(dY) + p * M + g);
 }
 
 // First point of every Morton unit (2 x 2 x 2 bins) that starts a run of that unit in
@@ -780,20 +540,43 @@ __global__ void k_unit_starts(Bricks brp, const float* __restrict__ xyz, int32_t
   }
 }
 
-// One CTA per brick.  Units without a recorded start take the next recorded one (a
-// suffix minimum; for a sorted batch this is exact, for any batch the starts become
-// non-decreasing from 0 to n, so the tiles below always partition the brick's points).  Every unit
-// then belongs to the largest aligned range of 2^L units (L <= lmax) holding at most ST
-// points; each such range becomes ceil(points / ST) tiles of consecutive points.
-__global__ void __launch_bounds__(1024) k_tile_list(Bricks brp, TrainWs ws, int lmax) {
+// One CTA per brick.  The brick's largest tile level lmax is the largest L <= lcap whose
+// block, mapped through any of the brick's grids, has a node box of at most capn nodes:
+// per grid axis, the image's extent in cells plus the box margin, one partial cell at
+// each end and the node past the last cell bound tile_box's count (0 when even one unit
+// is too large; such grids add their corners directly).  Units without a recorded start
+// take the next recorded one (a suffix minimum; for a sorted batch this is exact, for any
+// batch the starts become non-decreasing from 0 to n, so the tiles below always partition
+// the brick's points).  Every unit then belongs to the largest aligned range of 2^L units
+// (L <= lmax) holding at most ST points; each such range becomes ceil(points / ST) tiles
+// of consecutive points.
+__global__ void __launch_bounds__(1024) k_tile_list(Bricks brp, TrainWs ws, Model md, int capn, int lcap) {
   constexpr int UPT = kUnits / 1024;
   __shared__ Bricks br;
   __shared__ int32_t st[kUnits + 1];
   __shared__ int32_t wred[32];
   __shared__ int32_t gbase;
+  __shared__ int32_t s_lv;
+  if (threadIdx.x == 0) s_lv = lcap;
   load_bricks(brp, br);
-  __syncthreads();
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < md.M) {
+    const float* g = md.G + (int64_t)b * md.sG + 12 * tid;
+    const float hs = 0.5f * (float)(md.R - 1) * (2.f / (float)(1 << kUnitBits));   // cells per unit
+    int lv = 0;
+    for (int L = lcap; L > 0; --L) {
+      const float ext[3] = {(float)(1 << ((L + 2) / 3)), (float)(1 << ((L + 1) / 3)), (float)(1 << (L / 3))};
+      int nodes = 1;
+      for (int d = 0; d < 3; ++d) {
+        const float e = (fabsf(g[4 * d]) * ext[0] + fabsf(g[4 * d + 1]) * ext[1] + fabsf(g[4 * d + 2]) * ext[2]) * hs;
+        nodes *= min((int)ceilf(e + 0.01f) + 2, md.R);
+      }
+      if (nodes <= capn) { lv = L; break; }
+    }
+    atomicMin(&s_lv, lv);
+  }
+  __syncthreads();
+  const int lmax = s_lv;
   const int64_t o = br.off[b];
   const int32_t n = (int32_t)(br.off[b + 1] - o);
   const int32_t* us = ws.ustart + (int64_t)b * (kUnits + 1);
@@ -909,20 +692,28 @@ __device__ uint2 tile_box(uint32_t code, const float* __restrict__ g, int R) {
 }
 
 template <int C>
-__global__ void __launch_bounds__(SNT, 3)
-k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
+__global__ void __launch_bounds__(SNT, 1)
+k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  ScatSmem& s = *reinterpret_cast<ScatSmem*>(smraw);
+  ScatHead& h = *reinterpret_cast<ScatHead*>(smraw);
+  int32_t* acc = reinterpret_cast<int32_t*>(smraw + sizeof(ScatHead));
   __shared__ Bricks br;
-  __shared__ ScatTile cur_tile;
   load_bricks(brp, br);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int M = md.M, R = md.R;
-  for (int l = tid; l <= CCAP; l += SNT) s.cnt[l] = 0;
+  const ScatMap mp = scat_map(M);
+  const int ngrp = M >= 32 ? M >> 5 : 1;
+  constexpr int kNode = C * 32;                  // words of one node of a column group
+  constexpr uint32_t kNodeBytes = kNode * 4;
+  {  // the boxes start zeroed; every flush leaves them zeroed again
+    uint4* a4 = reinterpret_cast<uint4*>(acc);
+    for (int q = tid; q < ngrp * capn * kNode / 4; q += SNT) a4[q] = make_uint4(0u, 0u, 0u, 0u);
+  }
   const int ntiles = ws.tile_ctr[0];
-  const int64_t ntot = br.off[br.n];
   const int64_t gsz = (int64_t)R * R * R * C;
-  unsigned parity = 0;
+  int32_t* col = acc + mp.grp * capn * kNode + lane;         // this thread's column
+  const uint32_t col_s = su32(col);
+  constexpr uint32_t kNz = C == 2 ? 0x7fff7fffu : 0x7fffu;    // nonzero dL/dy
   for (;;) {
     // tiles are taken in list order (brick by brick, Morton order inside a brick), so
     // the CTAs on the GPU at one time work on neighbouring blocks of one brick
@@ -931,133 +722,138 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
       ScatTile T;
       T.start = 0; T.count = -1; T.code = 0;
       if (t < ntiles) T = ws.tiles[t];
-      cur_tile = T;
+      h.tile = T;
     }
-    __syncthreads();
-    const ScatTile T = cur_tile;
+    __syncthreads();   // also: the previous tile's flush has finished with h
+    const ScatTile T = h.tile;
     if (T.count < 0) break;
     const int b = (int)(T.code >> 20);
     const int64_t p0 = T.start;
     const int np = T.count;
     const float* Gb = md.G + (int64_t)b * md.sG;
-    for (int i = tid; i < M; i += SNT) s.tbox[i] = tile_box(T.code, Gb + 12 * i, R);
-    float px[PPT], py[PPT], pz[PPT];   // this thread's points (tid + 256 j), kept in registers
-    bool mine_in = true;               // every point of this thread lies in the tile's block
     const int lvl = (int)((T.code >> 16) & 15u);
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      const int p = tid + SNT * j;
-      px[j] = py[j] = pz[j] = 0.f;
-      if (p < np) {
-        px[j] = xyz[3 * (p0 + p)]; py[j] = xyz[3 * (p0 + p) + 1]; pz[j] = xyz[3 * (p0 + p) + 2];
-        mine_in &= (((morton_bin(px[j], py[j], pz[j]) >> 3) ^ (T.code & 0xffffu)) >> lvl) == 0u;
-      }
+    bool mine_in = true;   // every point of this thread lies in the tile's block
+    for (int p = tid; p < np; p += SNT) {
+      const float x = xyz[3 * (p0 + p)], y = xyz[3 * (p0 + p) + 1], z = xyz[3 * (p0 + p) + 2];
+      h.xs[p] = make_float4(x, y, z, 0.f);
+      mine_in &= (((morton_bin(x, y, z) >> 3) ^ (T.code & 0xffffu)) >> lvl) == 0u;
     }
-    const unsigned act = (1u << ((np + SNT - 1) / SNT)) - 1u;   // chunks holding points
-    // dL/dy of grid i is loaded one grid ahead, so its latency hides behind grid i-1
-    uint32_t dyn[PPT];
-    auto load_dy = [&](int i) {
-#pragma unroll
-      for (int j = 0; j < PPT; ++j) {
-        const int p = tid + SNT * j;
-        dyn[j] = 0u;
-        if (p < np) {
-          if (C == 2) dyn[j] = __ldg(reinterpret_cast<const unsigned int*>(ws.dY) + (int64_t)i * ntot + p0 + p);
-          else dyn[j] = (uint32_t)__bfloat16_as_ushort(ws.dY[(int64_t)i * ntot + p0 + p]);
-        }
-      }
-    };
-    load_dy(0);
-    // s.tbox; the block's boxes bound the points only if all of them lie in the block
-    // (always, for a Morton-sorted batch)
+    if (tid < M) {
+      h.box[tid] = tile_box(T.code, Gb + 12 * tid, R);
+      h.gmax[tid] = 0u;
+    }
+    // the block's boxes bound the points only if all of them lie in the block (always,
+    // for a Morton-sorted batch); otherwise points outside a box add their corners directly
     const bool in_block = __syncthreads_and(mine_in) != 0;
-    for (int i = 0; i < M; ++i) {
-      uint32_t dcur[PPT];
+    {  // largest |dL/dy| of every grid over the tile (eight loads in flight)
+      uint32_t mx = 0u;
+      for (int p = mp.pg; p < np; p += 8 * mp.npg) {
+        uint32_t d[8];
 #pragma unroll
-      for (int j = 0; j < PPT; ++j) dcur[j] = dyn[j];
-      if (i + 1 < M) load_dy(i + 1);
-      const uint2 tb = s.tbox[i];
-      if (in_block && tb.y == 0u) continue;   // the block lies outside grid i
+        for (int u = 0; u < 8; ++u) {
+          const int q = p + u * mp.npg;
+          d[u] = q < np ? dy_bits<C>(ws.dY, p0 + q, M, mp.g) & kNz : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mx = C == 2 ? __vmaxu2(mx, d[u]) : max(mx, d[u]);
+      }
+      if (C == 2) mx = max(mx & 0xffffu, mx >> 16);
+      if (mx) atomicMax(h.gmax + mp.g, mx);
+    }
+    __syncthreads();
+    const uint2 bx = h.box[mp.g];
+    const int nxb = (int)(bx.y & 0xffu), nyb = (int)((bx.y >> 8) & 0xffu), nzb = (int)((bx.y >> 16) & 0xffu);
+    const int lox = (int)(bx.x & 0xffu), loy = (int)((bx.x >> 8) & 0xffu), loz = (int)((bx.x >> 16) & 0xffu);
+    const int nodes = nxb * nyb * nzb;
+    const bool boxed = nodes > 0 && nodes <= capn;
+    const uint32_t mb = h.gmax[mp.g];
+    float inv;
+    const float scale = fixed_scale(mb, np, inv);
+    float* dFi = gr.dF + (int64_t)b * gr.sF + mp.g * gsz;
+    if (mb != 0u && (nodes > 0 || !in_block)) {
       float gi[12];
       {
-        const float4* g4 = reinterpret_cast<const float4*>(Gb + 12 * i);
+        const float4* g4 = reinterpret_cast<const float4*>(Gb + 12 * mp.g);
         const float4 a = __ldg(g4), c = __ldg(g4 + 1), d = __ldg(g4 + 2);
         gi[0] = a.x; gi[1] = a.y; gi[2] = a.z; gi[3] = a.w; gi[4] = c.x; gi[5] = c.y;
         gi[6] = c.z; gi[7] = c.w; gi[8] = d.x; gi[9] = d.y; gi[10] = d.z; gi[11] = d.w;
       }
-      float* dFi = gr.dF + (int64_t)b * gr.sF + i * gsz;
-      Box bx;
+      const uint32_t oy = (uint32_t)nxb * kNodeBytes, oz = (uint32_t)(nxb * nyb) * kNodeBytes;
+      const float hs = 0.5f * (float)(R - 1);
+      // dL/dy of the next SU points is requested while the current SU are processed
+      constexpr int SU = 4;
+      uint32_t dn[SU];
+      auto load_next = [&](int p) {
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        bx.lo[d] = (int)((tb.x >> (8 * d)) & 0xffu);
-        bx.n[d] = (int)((tb.y >> (8 * d)) & 0xffu);
-      }
-      bx.ncells = (bx.n[0] - 1) * (bx.n[1] - 1) * (bx.n[2] - 1);
-      bx.ok = in_block && bx.ncells <= CCAP && bx.n[0] * bx.n[1] * bx.n[2] <= NCAP;
-      if (bx.ok) {   // block-uniform
-        short id[PPT];
-        int rk[PPT];
-#pragma unroll
-        for (int j = 0; j < PPT; ++j) {
-          const int p = tid + SNT * j;
-          id[j] = -1;
-          rk[j] = -1;
-          if (p < np) {
-            float ux, uy, uz;
-            affine(gi, px[j], py[j], pz[j], ux, uy, uz);
-            const Cell c = make_cell(ux, uy, uz, R);
-            if (c.inside && (dcur[j] & 0x7fff7fffu)) {
-              const int lx = c.cx - bx.lo[0], ly = c.cy - bx.lo[1], lz = c.cz - bx.lo[2];
-              if (lx >= 0 && ly >= 0 && lz >= 0 && lx < bx.n[0] - 1 && ly < bx.n[1] - 1 && lz < bx.n[2] - 1) {
-                id[j] = (short)((lz * (bx.n[1] - 1) + ly) * (bx.n[0] - 1) + lx);
-                s.wg[p] = make_float4(c.wx, c.wy, c.wz, __uint_as_float(dcur[j]));
-                rk[j] = atomicAdd(s.cnt + id[j], 1);
-              } else {   // outside the block's box (rounding at its faces): add the corners directly
-                const float2 g = unpack_bf16(dcur[j]);
-                scatter_point(dFi, c, R, C, g.x, g.y);
-              }
-            }
-          }
+        for (int u = 0; u < SU; ++u) {
+          const int q = p + u * mp.npg;
+          dn[u] = q < np ? dy_bits<C>(ws.dY, p0 + q, M, mp.g) : 0u;
         }
-        box_pass<C>(s, bx, dFi, R, id, rk);
-        continue;
-      }
-      // the block's box is too large, or does not bound the points: exact boxes of the
-      // points, of each half, of each 256-point chunk, else the chunk's points add their
-      // corners directly
+      };
+      load_next(mp.pg);
+      for (int p = mp.pg; p < np; p += SU * mp.npg) {
+        uint32_t dc[SU];
 #pragma unroll
-      for (int j = 0; j < PPT; ++j) {
-        const int p = tid + SNT * j;
-        if (!((act >> j) & 1u)) continue;
-        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (p < np) {
+        for (int u = 0; u < SU; ++u) dc[u] = dn[u];
+        load_next(p + SU * mp.npg);
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+          const uint32_t d = dc[u];
+          if (!(d & kNz)) continue;   // zero dL/dy, or past the tile's last point
+          const float4 x = h.xs[p + u * mp.npg];
           float ux, uy, uz;
-          affine(gi, px[j], py[j], pz[j], ux, uy, uz);
-          const Cell c = make_cell(ux, uy, uz, R);
-          w = make_float4((float)c.cx + c.wx, (float)c.cy + c.wy, (float)c.cz + c.wz,
-                          __uint_as_float(c.inside ? dcur[j] : 0u));
-        }
-        s.wg[p] = w;
-      }
-      if (masked_pass<C>(s, act, dFi, R, parity)) continue;
-#pragma unroll
-      for (int h = 0; h < PPT / 2; ++h) {
-        const unsigned hm = (3u << (2 * h)) & act;
-        if (!hm) continue;
-        if (hm != act && masked_pass<C>(s, hm, dFi, R, parity)) continue;
-#pragma unroll
-        for (int c = 2 * h; c < 2 * h + 2; ++c) {
-          const unsigned cm = 1u << c;
-          if (!(act & cm)) continue;
-          if (cm != hm && masked_pass<C>(s, cm, dFi, R, parity)) continue;
-          const float4 w = s.wg[tid + SNT * c];
-          if (__float_as_uint(w.w) & 0x7fff7fffu) {
-            Cell cl;
-            cell_of(w, R, cl.cx, cl.cy, cl.cz);
-            cl.wx = w.x - (float)cl.cx; cl.wy = w.y - (float)cl.cy; cl.wz = w.z - (float)cl.cz;
-            const float2 g = unpack_bf16(__float_as_uint(w.w));
-            scatter_point(dFi, cl, R, C, g.x, g.y);
+          affine(gi, x.x, x.y, x.z, ux, uy, uz);
+          // Eq. 2's set-up as make_cell computes it; for points inside the grid s lies in
+          // [0, R-1] already (the rounding of fmaf is monotone), so no clamp is needed
+          if (!((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f))) continue;
+          Cell c;
+          const float sx = fmaf(ux, hs, hs), sy = fmaf(uy, hs, hs), sz = fmaf(uz, hs, hs);
+          c.cx = min((int)sx, R - 2); c.cy = min((int)sy, R - 2); c.cz = min((int)sz, R - 2);
+          c.wx = sx - (float)c.cx; c.wy = sy - (float)c.cy; c.wz = sz - (float)c.cz;
+          c.inside = true;
+          const float g0 = __uint_as_float(d << 16), g1 = __uint_as_float(d & 0xffff0000u);
+          const unsigned lx = (unsigned)(c.cx - lox), ly = (unsigned)(c.cy - loy), lz = (unsigned)(c.cz - loz);
+          if (boxed && lx < (unsigned)(nxb - 1) && ly < (unsigned)(nyb - 1) && lz < (unsigned)(nzb - 1)) {
+            const float ax = 1.f - c.wx, ay = 1.f - c.wy, az = 1.f - c.wz;
+            const float zy0 = az * ay, zy1 = az * c.wy, zy2 = c.wz * ay, zy3 = c.wz * c.wy;
+            const float gs0 = g0 * scale, gs1 = g1 * scale;
+            const uint32_t a0 = col_s + ((lz * (unsigned)nyb + ly) * (unsigned)nxb + lx) * kNodeBytes;
+            red_pair<C>(a0, zy0 * ax, zy0 * c.wx, gs0, gs1);
+            red_pair<C>(a0 + oy, zy1 * ax, zy1 * c.wx, gs0, gs1);
+            red_pair<C>(a0 + oz, zy2 * ax, zy2 * c.wx, gs0, gs1);
+            red_pair<C>(a0 + oy + oz, zy3 * ax, zy3 * c.wx, gs0, gs1);
+          } else {   // outside the tile's box (rounding at its faces, or an unsorted batch)
+            scatter_point(dFi, c, R, C, g0, C == 2 ? g1 : 0.f);
           }
+        }
+      }
+    }
+    __syncthreads();
+    // flush: every nonzero node of the grid's box into the float32 gradient grid with one
+    // atomic, summing the grid's columns (M < 32) and clearing them for the next tile
+    if (boxed && mb != 0u && (M >= 32 || lane < M)) {
+      const int step = M >= 32 ? mp.npg : SNW;   // M < 32: lanes >= M idle, warps split the nodes
+      const int n0 = M >= 32 ? mp.pg : (tid >> 5);
+      int qz = n0 / (nxb * nyb), qr = n0 - qz * nxb * nyb;
+      int qy = qr / nxb, qx = qr - qy * nxb;
+      for (int n = n0; n < nodes; n += step) {
+        int32_t s0 = 0, s1 = 0;
+        int32_t* q = acc + mp.grp * capn * kNode + n * kNode + lane;   // column lane = grid g's first
+        for (int sub = 0; sub < (M >= 32 ? 1 : 32 / M); ++sub) {
+          int32_t* qs = q + sub * M;
+          s0 += qs[0];
+          qs[0] = 0;
+          if (C == 2) { s1 += qs[32]; qs[32] = 0; }
+        }
+        if (s0 | s1) {
+          const int64_t node = ((int64_t)(loz + qz) * R + (loy + qy)) * R + lox + qx;
+          if (C == 2) atomicAdd(reinterpret_cast<float2*>(dFi) + node, make_float2((float)s0 * inv, (float)s1 * inv));
+          else atomicAdd(dFi + node, (float)s0 * inv);
+        }
+        qx += step;
+        while (qx >= nxb) {
+          qx -= nxb;
+          if (++qy == nyb) { qy = 0; ++qz; }
         }
       }
     }
@@ -1088,7 +884,6 @@ __global__ void __launch_bounds__(RNT) k_rec_dg(Model md, Bricks brp, TrainWs ws
   const int total = tm.first[br.n];
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int tb = blockIdx.x * per, te = min(total, tb + per);
-  const int64_t ntot = br.off[br.n];
   const int64_t gsz = (int64_t)R * R * R * C;
   const float hs = 0.5f * (float)(R - 1);
   float acc[12];
@@ -1133,11 +928,11 @@ __global__ void __launch_bounds__(RNT) k_rec_dg(Model md, Bricks brp, TrainWs ws
       if (!c.inside) continue;
       float g0, g1 = 0.f;
       if (C == 2) {
-        const float2 d = unpack_bf16(__ldg(reinterpret_cast<const unsigned int*>(ws.dY) + (int64_t)gi * ntot + p0 + p));
+        const float2 d = unpack_bf16(__ldg(reinterpret_cast<const unsigned int*>(ws.dY) + (p0 + p) * M + gi));
         g0 = d.x;
         g1 = d.y;
       } else {
-        g0 = __bfloat162float(ws.dY[(int64_t)gi * ntot + p0 + p]);
+        g0 = __bfloat162float(ws.dY[(p0 + p) * M + gi]);
       }
       const int64_t nb = ((int64_t)c.cz * R + c.cy) * R + c.cx;
       float a[8];
@@ -1173,6 +968,23 @@ int occupancy(const void* kern, int threads, size_t smem) {
   return n;
 }
 
+// Dynamic shared memory of k_scat for boxes of capn nodes, and the largest capn that
+// the device's per-block limit allows beside the kernel's static shared memory.
+size_t scat_smem(int M, int C, int capn) {
+  const int ngrp = M >= 32 ? M / 32 : 1;
+  return sizeof(ScatHead) + (size_t)ngrp * capn * C * 128;
+}
+int scat_capn(int M, int C) {
+  int dev = 0, optin = 0, stat = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, (const void*)k_scat<2>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
+  const int ngrp = M >= 32 ? M / 32 : 1;
+  const long long room = (long long)optin - stat - (long long)sizeof(ScatHead);
+  return room > 0 ? (int)(room / ((long long)ngrp * C * 128)) : 0;
+}
+
 template <int K>
 cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
                            const TrainWs& ws, const float* xyz, const float* target, const KernelMark* mark) {
@@ -1192,7 +1004,7 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     const int bx = (int)std::min<int64_t>((nmax + 255) / 256, 4 * L.num_sms / std::max(1, br.n) + 1);
     k_unit_starts<<<dim3(bx, br.n), 256, 0, L.stream>>>(br, xyz, ws.ustart);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_tile_list<<<br.n, 1024, 0, L.stream>>>(br, ws, scat_lmax(md.R));
+    k_tile_list<<<br.n, 1024, 0, L.stream>>>(br, ws, md, scat_capn(md.M, md.C), kTileLevelCap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -1219,19 +1031,16 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     mark_stop(1);
   }
   {
-    const size_t smem = sizeof(ScatSmem);
+    const int capn = scat_capn(md.M, md.C);
+    if (capn < 8) return cudaErrorInvalidConfiguration;
+    const size_t smem = scat_smem(md.M, md.C, capn);
+    const void* kern = md.C == 2 ? (const void*)k_scat<2> : (const void*)k_scat<1>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    const int grid = L.num_sms * occupancy(kern, SNT, smem);
     mark_start(2);
-    if (md.C == 2) {
-      if ((e = cudaFuncSetAttribute(k_scat<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return e;
-      const int grid = L.num_sms * occupancy((const void*)k_scat<2>, SNT, smem);
-      k_scat<2><<<grid, SNT, smem, L.stream>>>(md, gr, br, ws, xyz);
-    } else {
-      if ((e = cudaFuncSetAttribute(k_scat<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return e;
-      const int grid = L.num_sms * occupancy((const void*)k_scat<1>, SNT, smem);
-      k_scat<1><<<grid, SNT, smem, L.stream>>>(md, gr, br, ws, xyz);
-    }
+    if (md.C == 2) k_scat<2><<<grid, SNT, smem, L.stream>>>(md, gr, br, ws, xyz, capn);
+    else k_scat<1><<<grid, SNT, smem, L.stream>>>(md, gr, br, ws, xyz, capn);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark_stop(2);
   }
