@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <type_traits>
 
 namespace srn {
 namespace {
@@ -35,96 +36,7 @@ __device__ __forceinline__ Tv warp_sum(Tv v) {
   return v;
 }
 
-// =============================================================================== k_enc
-constexpr int ET = 128;
-constexpr int ENT = 256;
-
-template <int K, bool DENS>
-__global__ void __launch_bounds__(ENT, 4)
-k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
-  __shared__ TileMap tm;
-  __shared__ Bricks br;
-  __shared__ float4 xs[ET];
-  __shared__ __align__(16) float gs[kMaxGrids * 12];
-  __shared__ float dets[kMaxGrids];
-  __shared__ float rhos[2][ET];
-  __shared__ uint32_t ys[ET][K / 2 + 1];   // bf16 pairs; odd row pitch: conflict-free column writes
-  load_bricks(brp, br);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int M = md.M, C = md.C, R = md.R;
-  if (tid == 0) build_tile_map(br, ET, tm);
-  __syncthreads();
-  const int total = tm.first[br.n];
-  const int per = (total + gridDim.x - 1) / gridDim.x;
-  const int tb = blockIdx.x * per, te = min(total, tb + per);
-  double sum_rho = 0.0;
-  int cur = -1;
-  auto flush = [&](int b) {
-    if (!DENS) return;
-    double s = warp_sum(sum_rho);
-    if (lane == 0) atomicAdd(ws.acc + b * kAccPerBrick + ACC_SUM_RHO, s);
-    sum_rho = 0.0;
-  };
-  uint32_t* Y32 = reinterpret_cast<uint32_t*>(ws.Y);
-  for (int tile = tb; tile < te; ++tile) {
-    const int b = brick_of_tile(tm, br.n, tile, cur);
-    if (b != cur) {
-      if (cur >= 0) flush(cur);
-      __syncthreads();
-      cur = b;
-      const float* G = md.G + (int64_t)b * md.sG;
-      for (int c = tid; c < M * 12; c += ENT) gs[c] = G[c];
-      if (tid < M) dets[tid] = det3(G + 12 * tid);
-      __syncthreads();
-    }
-    const int64_t p0 = br.off[b] + (int64_t)(tile - tm.first[b]) * ET;
-    const int np = (int)min((int64_t)ET, br.off[b + 1] - p0);
-    if (tid < ET) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (tid < np) v = make_float4(xyz[3 * (p0 + tid)], xyz[3 * (p0 + tid) + 1], xyz[3 * (p0 + tid) + 2], 0.f);
-      xs[tid] = v;
-    }
-    __syncthreads();
-    {
-      const __nv_bfloat16* Fb = md.F16 + (int64_t)b * md.sF;
-      const int64_t gsz = (int64_t)R * R * R * C;
-      const int p = (warp & 3) * 32 + lane, gsub = warp >> 2;
-      const float4 pt = xs[p];
-      const bool valid = p < np;
-      float rho = 0.f;
-#pragma unroll 4
-      for (int i = gsub; i < M; i += 2) {
-        float ux, uy, uz;
-        {
-          const float4* g4 = reinterpret_cast<const float4*>(gs + 12 * i);
-          const float4 a = g4[0], c = g4[1], d = g4[2];
-          ux = fmaf(a.x, pt.x, fmaf(a.y, pt.y, fmaf(a.z, pt.z, a.w)));
-          uy = fmaf(c.x, pt.x, fmaf(c.y, pt.y, fmaf(c.z, pt.z, c.w)));
-          uz = fmaf(d.x, pt.x, fmaf(d.y, pt.y, fmaf(d.z, pt.z, d.w)));
-        }
-        const Cell c = make_cell(ux, uy, uz, R);
-        float f0 = 0.f, f1 = 0.f;
-        if (valid && c.inside) trilinear_bf16_any(Fb + i * gsz, c, R, C, f0, f1);
-        if (C == 2) ys[p][i] = pack_bf16(f0, f1);
-        else reinterpret_cast<__nv_bfloat16*>(ys[p])[i] = __float2bfloat16_rn(f0);
-        if (DENS && valid) rho += dets[i] * flat_top(ux, uy, uz, md.p);
-      }
-      if (DENS) rhos[gsub][p] = rho;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < np * (K / 2); idx += ENT) {
-      const int p = idx / (K / 2), w = idx % (K / 2);
-      Y32[(p0 + p) * (K / 2) + w] = ys[p][w];
-    }
-    if (DENS && tid < np) {
-      const float r = rhos[0][tid] + rhos[1][tid];
-      ws.rho[p0 + tid] = r;
-      sum_rho += (double)r;
-    }
-    __syncthreads();
-  }
-  if (cur >= 0) flush(cur);
-}
+constexpr int ET = 128;   // points per decoder tile (k_mlp, k_mlp_tc)
 
 // =============================================================================== k_mlp
 constexpr int T = 128;
@@ -860,6 +772,245 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
   }
 }
 
+// =============================================================================== k_enc
+// Encoder (Eq. 1-3) and the feature density of Eq. 7 on the scatter's tiles.  Lane l of a
+// warp takes grid l of a group of 32 (ScatMap).  Each grid's node box of the tile's block
+// is staged in shared memory as BF16 node values (C per entry), node by node with one
+// column per lane, so the eight corner reads of a warp fall in 32 different banks and the
+// warp's features of one point form one coalesced store of Y.  Points outside their box
+// (rounding at its faces; an unsorted batch) and grids whose box does not fit read the
+// corners from global memory.  The density rho of a point sums det(A_i) E_i over the
+// grids: with M >= 32 the warp adds its 32 lanes' terms as fixed-point integers (one
+// reduction instruction; a power-of-two scale per brick keeps every term below 2^21),
+// with M < 32 by shuffles, and the groups' integer partial sums meet in the point's staged
+// slot (a shared-memory integer reduction).
+struct EncHead {
+  float4 xs[ST];                // the tile's points; .w collects rho
+  uint2 box[kMaxGrids];         // node box of the tile's block per grid (as in the scatter)
+  float gs[kMaxGrids * 12];     // the brick's transforms
+  float det[kMaxGrids];         // their determinants
+  float dscale, dinv;           // fixed-point scale of the density terms and its inverse
+  ScatTile tile;
+};
+template <int C>
+using EncNode = std::conditional_t<C == 2, uint32_t, uint16_t>;   // one node: C bf16 values
+
+// Packed float pairs (two channels at once).
+__device__ __forceinline__ unsigned long long f2_bits(float lo, float hi) {
+  return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ unsigned long long bf2_bits(uint32_t v) {   // bf16x2 -> f32x2
+  return f2_bits(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+}
+// a + w (b - a) on both halves
+__device__ __forceinline__ unsigned long long lerp2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long w) {
+  unsigned long long d, r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(b), "l"(a));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(w), "l"(d), "l"(a));
+  return r;
+}
+
+// One staged node (C bf16 values) at shared address a + OFF.
+template <int C, int OFF>
+__device__ __forceinline__ uint32_t enc_node(uint32_t a) {
+  uint32_t v;
+  if constexpr (C == 2) asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+  else asm volatile("ld.shared.u16 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+  return v;
+}
+// Eq. 2 from the grid in global memory (a point outside its tile's box), packed as Y.
+template <int C>
+__device__ __noinline__ uint32_t enc_global(const __nv_bfloat16* Fi, Cell c, int R) {
+  float f0 = 0.f, f1 = 0.f;
+  trilinear_bf16_any(Fi, c, R, C, f0, f1);
+  return C == 2 ? pack_bf16(f0, f1) : (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f0));
+}
+
+// P10: the paper's flat-top exponent p = 10 at compile time (DENS only).
+template <int C, bool DENS, bool P10>
+__global__ void __launch_bounds__(SNT, 2)
+k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn) {
+  using E = EncNode<C>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  EncHead& h = *reinterpret_cast<EncHead*>(smraw);
+  E* boxes = reinterpret_cast<E*>(smraw + sizeof(EncHead));   // [group][capn][32 columns]
+  __shared__ Bricks br;
+  load_bricks(brp, br);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int M = md.M, R = md.R;
+  const ScatMap mp = scat_map(M);
+  const int ntiles = ws.tile_ctr[0];
+  const int64_t gsz = (int64_t)R * R * R * C;
+  E* col = boxes + mp.grp * capn * 32 + lane;             // this thread's column
+  constexpr uint32_t kRow = 32 * sizeof(E);              // bytes of one node row
+  const float hs = 0.5f * (float)(R - 1);
+  // staging: M >= 32, the warps of a group split the nodes of their grids; M < 32, every
+  // lane fills its own column and all warps split the nodes
+  const int n0 = M >= 32 ? mp.pg : warp, nstep = M >= 32 ? mp.npg : SNW;
+  double sum_rho = 0.0;
+  int cur = -1;
+  auto flush = [&](int b) {
+    double s = warp_sum(sum_rho);
+    if (lane == 0) atomicAdd(ws.acc + b * kAccPerBrick + ACC_SUM_RHO, s);
+    sum_rho = 0.0;
+  };
+  for (;;) {
+    if (tid == 0) {
+      const int t = atomicAdd(ws.tile_ctr + 2, 1);
+      ScatTile T;
+      T.start = 0; T.count = -1; T.code = 0;
+      if (t < ntiles) T = ws.tiles[t];
+      h.tile = T;
+    }
+    __syncthreads();   // also: the previous tile is done with h and the boxes
+    const ScatTile T = h.tile;
+    if (T.count < 0) break;
+    const int b = (int)(T.code >> 20);
+    const float* Gb = md.G + (int64_t)b * md.sG;
+    if (b != cur) {
+      if (DENS && cur >= 0) flush(cur);
+      cur = b;
+      for (int c = tid; c < M * 12; c += SNT) h.gs[c] = Gb[c];
+      if (DENS && warp == 0) {
+        float m = 0.f;
+        for (int i = lane; i < M; i += 32) {
+          const float d = det3(Gb + 12 * i);
+          h.det[i] = d;
+          m = fmaxf(m, fabsf(d));
+        }
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        if (lane == 0) {   // |det E| 2^S < 2^21 for every grid (E <= 1)
+          int ex = 0;
+          frexpf(m, &ex);   // m < 2^ex
+          const int S = max(-100, min(100, 21 - ex));
+          h.dscale = ldexpf(1.f, S);
+          h.dinv = ldexpf(1.f, -S);
+        }
+      }
+    }
+    const int64_t p0 = T.start;
+    const int np = T.count;
+    const int lvl = (int)((T.code >> 16) & 15u);
+    bool mine_in = true;
+    for (int p = tid; p < np; p += SNT) {
+      const float x = xyz[3 * (p0 + p)], y = xyz[3 * (p0 + p) + 1], z = xyz[3 * (p0 + p) + 2];
+      h.xs[p] = make_float4(x, y, z, 0.f);
+      mine_in &= (((morton_bin(x, y, z) >> 3) ^ (T.code & 0xffffu)) >> lvl) == 0u;
+    }
+    if (tid < M) h.box[tid] = tile_box(T.code, Gb + 12 * tid, R);
+    const bool in_block = __syncthreads_and(mine_in) != 0;
+    const uint2 bx = h.box[mp.g];
+    const int nxb = (int)(bx.y & 0xffu), nyb = (int)((bx.y >> 8) & 0xffu), nzb = (int)((bx.y >> 16) & 0xffu);
+    const int lox = (int)(bx.x & 0xffu), loy = (int)((bx.x >> 8) & 0xffu), loz = (int)((bx.x >> 16) & 0xffu);
+    const int nodes = nxb * nyb * nzb;
+    const bool boxed = nodes > 0 && nodes <= capn;
+    const E* Fg = reinterpret_cast<const E*>(md.F16 + (int64_t)b * md.sF + mp.g * gsz);
+    if (boxed) {   // stage the grid's box, four node loads in flight
+      int qz = n0 / (nxb * nyb), qr = n0 - qz * nxb * nyb;
+      int qy = qr / nxb, qx = qr - qy * nxb;
+      for (int n = n0; n < nodes; n += 4 * nstep) {
+        E v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[u] = 0;
+          if (n + u * nstep < nodes) v[u] = __ldg(Fg + ((int64_t)(loz + qz) * R + (loy + qy)) * R + lox + qx);
+          qx += nstep;
+          while (qx >= nxb) {
+            qx -= nxb;
+            if (++qy == nyb) { qy = 0; ++qz; }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (n + u * nstep < nodes) col[(n + u * nstep) * 32] = v[u];
+      }
+    }
+    float gi[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) gi[j] = h.gs[12 * mp.g + j];
+    const float dq = DENS ? h.det[mp.g] * h.dscale : 0.f;   // det E 2^S + kMagic: round(det E 2^S) in the low bits
+    const float dinv = DENS ? h.dinv : 0.f;   // (the slots start at integer 0: xs[p].w = 0.f)
+    __syncthreads();
+    const uint32_t col_s = su32(col);
+    const uint32_t oy = (uint32_t)nxb * kRow, oz = (uint32_t)(nxb * nyb) * kRow;   // bytes
+    E* Yt = reinterpret_cast<E*>(ws.Y) + p0 * M + mp.g;
+    const __nv_bfloat16* Fi = md.F16 + (int64_t)b * md.sF + mp.g * gsz;
+    // the warp steps through its points together (M < 32: its 32/M lane groups take
+    // consecutive points), so the density reductions always see the whole warp
+    const int sub = M >= 32 ? 0 : lane / M;
+#pragma unroll 2
+    for (int pb = mp.pg - sub; pb < np; pb += mp.npg) {
+      const int p = pb + sub;
+      const bool valid = p < np;
+      const float4 x = h.xs[valid ? p : 0];
+      float ux, uy, uz;
+      affine(gi, x.x, x.y, x.z, ux, uy, uz);
+      if constexpr (DENS) {   // det E 2^S as an integer; the warp's (group's) sum into the point's slot
+        const float t = valid ? flat_top(ux, uy, uz, P10 ? 10 : md.p) : 0.f;
+        int32_t v = __float_as_int(fmaf(t, dq, kMagic)) - kMagicBits;
+        if (M >= 32) {
+          v = __reduce_add_sync(0xffffffffu, v);
+          if (lane == 0) red_s32<0>(su32(&h.xs[p].w), v);
+        } else {
+          for (int o = M >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (valid && lane % M == 0) red_s32<0>(su32(&h.xs[p].w), v);
+        }
+      }
+      if (!valid) continue;
+      uint32_t yv = 0u;
+      if ((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f)) {
+        // Eq. 2's set-up as make_cell computes it (no clamp needed inside the grid)
+        Cell c;
+        const float sx = fmaf(ux, hs, hs), sy = fmaf(uy, hs, hs), sz = fmaf(uz, hs, hs);
+        c.cx = min((int)sx, R - 2); c.cy = min((int)sy, R - 2); c.cz = min((int)sz, R - 2);
+        c.wx = sx - (float)c.cx; c.wy = sy - (float)c.cy; c.wz = sz - (float)c.cz;
+        c.inside = true;
+        const unsigned lx = (unsigned)(c.cx - lox), ly = (unsigned)(c.cy - loy), lz = (unsigned)(c.cz - loz);
+        if (boxed && lx < (unsigned)(nxb - 1) && ly < (unsigned)(nyb - 1) && lz < (unsigned)(nzb - 1)) {
+          const uint32_t a0 = col_s + ((lz * (unsigned)nyb + ly) * (unsigned)nxb + lx) * kRow;
+          const uint32_t a1 = a0 + oy, a2 = a0 + oz, a3 = a2 + oy;
+          if constexpr (C == 2) {
+            const unsigned long long wx = f2_bits(c.wx, c.wx), wy = f2_bits(c.wy, c.wy), wz = f2_bits(c.wz, c.wz);
+            const unsigned long long e0 = lerp2(bf2_bits(enc_node<C, 0>(a0)), bf2_bits(enc_node<C, kRow>(a0)), wx);
+            const unsigned long long e1 = lerp2(bf2_bits(enc_node<C, 0>(a1)), bf2_bits(enc_node<C, kRow>(a1)), wx);
+            const unsigned long long e2 = lerp2(bf2_bits(enc_node<C, 0>(a2)), bf2_bits(enc_node<C, kRow>(a2)), wx);
+            const unsigned long long e3 = lerp2(bf2_bits(enc_node<C, 0>(a3)), bf2_bits(enc_node<C, kRow>(a3)), wx);
+            const unsigned long long f = lerp2(lerp2(e0, e1, wy), lerp2(e2, e3, wy), wz);
+            yv = pack_bf16(__uint_as_float((uint32_t)f), __uint_as_float((uint32_t)(f >> 32)));
+          } else {
+            auto v = [](uint32_t q) { return __uint_as_float(q << 16); };
+            const float v0 = v(enc_node<C, 0>(a0)), v1 = v(enc_node<C, kRow>(a0));
+            const float v2 = v(enc_node<C, 0>(a1)), v3 = v(enc_node<C, kRow>(a1));
+            const float v4 = v(enc_node<C, 0>(a2)), v5 = v(enc_node<C, kRow>(a2));
+            const float v6 = v(enc_node<C, 0>(a3)), v7 = v(enc_node<C, kRow>(a3));
+            const float e0 = fmaf(c.wx, v1 - v0, v0), e1 = fmaf(c.wx, v3 - v2, v2);
+            const float e2 = fmaf(c.wx, v5 - v4, v4), e3 = fmaf(c.wx, v7 - v6, v6);
+            const float f01 = fmaf(c.wy, e1 - e0, e0), f23 = fmaf(c.wy, e3 - e2, e2);
+            yv = __bfloat16_as_ushort(__float2bfloat16_rn(fmaf(c.wz, f23 - f01, f01)));
+          }
+        } else {   // outside the tile's box: the corners from global memory
+          yv = enc_global<C>(Fi, c, R);
+        }
+      }
+      Yt[p * M] = (E)yv;
+    }
+    if constexpr (DENS) {
+      __syncthreads();
+      for (int p = tid; p < np; p += SNT) {
+        const float rho = (float)__float_as_int(h.xs[p].w) * dinv;   // the slot holds sum det E 2^S
+        ws.rho[p0 + p] = rho;
+        sum_rho += (double)rho;
+      }
+    }
+  }
+  if (DENS && cur >= 0) flush(cur);
+}
+
 // =============================================================================== k_rec_dg
 // dL/dG through the features (SRN_REC_DG), from the decoder's dL/dy: per point and
 // grid, dL/du = (R-1)/2 sum_c dL/dy_c de_c/ds (Eq. 2 differentiated inside the cell,
@@ -985,6 +1136,22 @@ int scat_capn(int M, int C) {
   return room > 0 ? (int)(room / ((long long)ngrp * C * 128)) : 0;
 }
 
+// The same for k_enc, at two CTAs per SM.
+size_t enc_smem(int M, int C, int capn) {
+  const int ngrp = M >= 32 ? M / 32 : 1;
+  return sizeof(EncHead) + (size_t)ngrp * capn * 32 * (C == 2 ? 4 : 2);
+}
+int enc_capn(int M, int C) {
+  int dev = 0, per_sm = 0, stat = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, (const void*)k_enc<2, true, true>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
+  const int ngrp = M >= 32 ? M / 32 : 1;
+  const long long room = (long long)per_sm / 2 - 1024 - stat - (long long)sizeof(EncHead);
+  return room > 0 ? (int)(room / ((long long)ngrp * 32 * (C == 2 ? 4 : 2))) : 0;
+}
+
 template <int K>
 cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
                            const TrainWs& ws, const float* xyz, const float* target, const KernelMark* mark) {
@@ -1000,19 +1167,29 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     if (nmax > INT32_MAX) return cudaErrorInvalidValue;
     if ((e = cudaMemsetAsync(ws.ustart, 0xff, sizeof(int32_t) * (kUnits + 1) * br.n, L.stream)) != cudaSuccess)
       return e;
-    if ((e = cudaMemsetAsync(ws.tile_ctr, 0, 2 * sizeof(int32_t), L.stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws.tile_ctr, 0, 3 * sizeof(int32_t), L.stream)) != cudaSuccess) return e;
     const int bx = (int)std::min<int64_t>((nmax + 255) / 256, 4 * L.num_sms / std::max(1, br.n) + 1);
     k_unit_starts<<<dim3(bx, br.n), 256, 0, L.stream>>>(br, xyz, ws.ustart);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_tile_list<<<br.n, 1024, 0, L.stream>>>(br, ws, md, scat_capn(md.M, md.C), kTileLevelCap);
+    const int cap = std::min(scat_capn(md.M, md.C), enc_capn(md.M, md.C));   // both kernels' boxes fit
+    if (cap < 8) return cudaErrorInvalidConfiguration;
+    k_tile_list<<<br.n, 1024, 0, L.stream>>>(br, ws, md, cap, kTileLevelCap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
-    const void* kern = dens ? (const void*)k_enc<K, true> : (const void*)k_enc<K, false>;
-    const int grid = std::min(tiles, L.num_sms * occupancy(kern, ENT, 0));
+    const int capn = enc_capn(md.M, md.C);
+    const size_t smem = enc_smem(md.M, md.C, capn);
+    const bool p10 = md.p == 10;
+    const void* kern = md.C == 2 ? (dens ? (p10 ? (const void*)k_enc<2, true, true> : (const void*)k_enc<2, true, false>)
+                                         : (const void*)k_enc<2, false, true>)
+                                 : (dens ? (p10 ? (const void*)k_enc<1, true, true> : (const void*)k_enc<1, true, false>)
+                                         : (const void*)k_enc<1, false, true>);
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    const int grid = L.num_sms * occupancy(kern, SNT, smem);
     mark_start(0);
-    if (dens) k_enc<K, true><<<grid, ENT, 0, L.stream>>>(md, br, ws, xyz);
-    else k_enc<K, false><<<grid, ENT, 0, L.stream>>>(md, br, ws, xyz);
+    void* args[] = {(void*)&md, (void*)&br, (void*)&ws, (void*)&xyz, (void*)&capn};
+    if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(SNT), args, smem, L.stream)) != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark_stop(0);
   }
