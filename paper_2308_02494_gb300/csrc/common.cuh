@@ -71,6 +71,7 @@ struct TrainWs {
   struct ScatTile* tiles;  // scatter tiles (BF16 training pass)
   int32_t* tile_ctr;  // [0] tiles written, [1] next tile to take
   const struct BrickSched* sched;   // per-brick training routine, or NULL (caller's flags)
+  float eps;          // the density loss's epsilon (Eq. 8-9)
 };
 
 // A scatter tile: `count` (<= 1024) consecutive points of one brick, all in the aligned

@@ -107,6 +107,9 @@ __global__ void __launch_bounds__(ST) k_density_scalar(Bricks br, TrainWs ws, fl
 constexpr int DT = 128;   // points per tile
 constexpr int DNT = 256;  // threads
 
+static_assert(sizeof(TileMap) + DT * (sizeof(float4) + sizeof(float)) + kMaxGrids * 12 * sizeof(float) +
+                  DNT * sizeof(double) + 1024 <= kDensityCtaSmem,
+              "k_density_grad's shared memory must fit beside the scatter");
 __global__ void __launch_bounds__(DNT, 4)
 k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, float eps) {
   __shared__ TileMap tm;
@@ -479,7 +482,7 @@ int blocks_for(int64_t n, int threads, int num_sms, int per_sm) {
 }  // namespace
 
 cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, const TrainWs& ws,
-                           const float* xyz, float eps) {
+                           const float* xyz, float eps, int ctas_per_sm) {
   const int64_t total = br.off[br.n];
   if (total == 0) return cudaSuccess;
   int stiles = 0;
@@ -490,7 +493,7 @@ cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, c
   if (e != cudaSuccess) return e;
   int tiles = 0;
   for (int b = 0; b < br.n; ++b) tiles += (int)((br.off[b + 1] - br.off[b] + DT - 1) / DT);
-  const int grid = tiles < 4 * L.num_sms ? tiles : 4 * L.num_sms;   // 4 x 8 warps per SM
+  const int grid = tiles < ctas_per_sm * L.num_sms ? tiles : ctas_per_sm * L.num_sms;   // 8 warps each
   k_density_grad<<<grid, DNT, 0, L.stream>>>(md, br, ws, xyz, eps);
   return cudaGetLastError();
 }

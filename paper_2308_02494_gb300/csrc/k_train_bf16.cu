@@ -1126,13 +1126,16 @@ size_t scat_smem(int M, int C, int capn) {
   return sizeof(ScatHead) + (size_t)ngrp * capn * C * 128;
 }
 int scat_capn(int M, int C) {
-  int dev = 0, optin = 0, stat = 0;
+  int dev = 0, optin = 0, per_sm = 0, stat = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, (const void*)k_scat<2>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
   const int ngrp = M >= 32 ? M / 32 : 1;
-  const long long room = (long long)optin - stat - (long long)sizeof(ScatHead);
+  // leave room for one CTA of the density pass that may run beside the scatter
+  const long long block = std::min<long long>(optin, (long long)per_sm - 1024 - kDensityCtaSmem);
+  const long long room = block - stat - (long long)sizeof(ScatHead);
   return room > 0 ? (int)(room / ((long long)ngrp * C * 128)) : 0;
 }
 
@@ -1154,7 +1157,8 @@ int enc_capn(int M, int C) {
 
 template <int K>
 cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
-                           const TrainWs& ws, const float* xyz, const float* target, const KernelMark* mark) {
+                           const TrainWs& ws, const float* xyz, const float* target, const KernelMark* mark,
+                           const SideStream* side) {
   auto mark_start = [&](int k) { if (mark && mark->which == k) cudaEventRecord(mark->start, L.stream); };
   auto mark_stop = [&](int k) { if (mark && mark->which == k) cudaEventRecord(mark->stop, L.stream); };
   int tiles = 0;
@@ -1207,6 +1211,12 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark_stop(1);
   }
+  if (dens && side) {   // the density passes beside the scatter
+    if ((e = cudaEventRecord(side->fork, L.stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side->stream, side->fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_density(Launch{side->stream, L.num_sms}, md, br, ws, xyz, ws.eps, 1)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(side->join, side->stream)) != cudaSuccess) return e;
+  }
   {
     const int capn = scat_capn(md.M, md.C);
     if (capn < 8) return cudaErrorInvalidConfiguration;
@@ -1227,18 +1237,20 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     else k_rec_dg<1><<<grid, RNT, 0, L.stream>>>(md, br, ws, xyz);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  if (dens && side && (e = cudaStreamWaitEvent(L.stream, side->join, 0)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
 }  // namespace
 
 cudaError_t launch_train_bf16(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
-                              const TrainWs& ws, const float* xyz, const float* target, const KernelMark* mark) {
+                              const TrainWs& ws, const float* xyz, const float* target, const KernelMark* mark,
+                              const SideStream* side) {
   switch (md.K) {
-    case 16: return launch_train_k<16>(L, dens, md, gr, br, ws, xyz, target, mark);
-    case 32: return launch_train_k<32>(L, dens, md, gr, br, ws, xyz, target, mark);
-    case 64: return launch_train_k<64>(L, dens, md, gr, br, ws, xyz, target, mark);
-    case 128: return launch_train_k<128>(L, dens, md, gr, br, ws, xyz, target, mark);
+    case 16: return launch_train_k<16>(L, dens, md, gr, br, ws, xyz, target, mark, side);
+    case 32: return launch_train_k<32>(L, dens, md, gr, br, ws, xyz, target, mark, side);
+    case 64: return launch_train_k<64>(L, dens, md, gr, br, ws, xyz, target, mark, side);
+    case 128: return launch_train_k<128>(L, dens, md, gr, br, ws, xyz, target, mark, side);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -23,9 +23,17 @@ struct KernelMark {
   int which;
   cudaEvent_t start, stop;
 };
+// A second stream for work that runs beside the scatter: with `dens`, the density
+// passes (which need the decoder's h and the encoder's rho, and nothing of the scatter)
+// run there, forked after the decoder and joined before the pass returns; one CTA per SM
+// of them fits beside the scatter's CTA.
+struct SideStream {
+  cudaStream_t stream;
+  cudaEvent_t fork, join;
+};
 cudaError_t launch_train_bf16(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
                               const TrainWs& ws, const float* xyz, const float* target,
-                              const KernelMark* mark = nullptr);
+                              const KernelMark* mark = nullptr, const SideStream* side = nullptr);
 // The decoder kernel of the BF16 training pass on the tcgen05 tensor cores (K = 128).
 cudaError_t launch_mlp_tc(const Launch& L, const Model& md, const Grads& gr, const Bricks& br, const TrainWs& ws,
                           const float* target);
@@ -36,7 +44,9 @@ cudaError_t launch_query_fp32(const Launch& L, QueryMode mode, const Model& md, 
 
 // Density loss (Eq. 7-9) second and third passes, and the per-brick finalisation.
 cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, const TrainWs& ws,
-                           const float* xyz, float eps);
+                           const float* xyz, float eps, int ctas_per_sm = 4);
+// Shared memory a CTA of the third density pass needs on its SM (static + reserved).
+constexpr int kDensityCtaSmem = 16 * 1024;
 cudaError_t launch_finalize(const Launch& L, const Bricks& br, const Model& md, const TrainWs& ws,
                             bool density, float* dG, int64_t sdG, double* losses);
 

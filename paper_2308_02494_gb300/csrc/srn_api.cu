@@ -166,6 +166,8 @@ struct srn_handle {
   size_t ev_next = 0;
   double timed_ms = 0.0;
   int64_t timed_launches = 0;
+  // BF16 training: a second stream for the density passes beside the scatter
+  srn::SideStream side{nullptr, nullptr, nullptr};
 
   srn::StepState* state() const { return reinterpret_cast<srn::StepState*>(ws + wl.state); }
   srn::BrickSched* sched() const { return reinterpret_cast<srn::BrickSched*>(ws + wl.sched); }
@@ -192,6 +194,7 @@ struct srn_handle {
     w.tiles = reinterpret_cast<srn::ScatTile*>(ws + wl.tiles);
     w.tile_ctr = reinterpret_cast<int32_t*>(ws + wl.tile_ctr);
     w.sched = nullptr;
+    w.eps = cfg.density_eps;
     return w;
   }
   srn::Model model() const {
@@ -292,7 +295,7 @@ srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn
     e = srn::launch_forward_bf16(L, md, br, xyz, out);
   else
     e = srn::launch_train_bf16(L, mode == srn::kTrainDensity, md, gr, br, ws, xyz, target,
-                               timed && time_kernel ? &mark : nullptr);
+                               timed && time_kernel ? &mark : nullptr, h->side.stream ? &h->side : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "query kernel");
   if (timed) {
     if (time_pass) cudaEventRecord(h->ev_stop[slot], L.stream);
@@ -321,7 +324,7 @@ srn_status do_backward(srn_handle* h, void* stream, const float* xyz, const floa
   srn::TrainWs tws = h->train_ws();
   tws.sched = sched;
   tws.rec_dg = rec_dg;
-  if (dens) {
+  if (dens && !(h->cfg.precision == SRN_BF16 && h->side.stream)) {   // else run beside the BF16 scatter
     e = srn::launch_density(L, md, br, tws, xyz, h->cfg.density_eps);
     if (e != cudaSuccess) return cuda_fail(e, "density kernels");
   }
@@ -445,6 +448,15 @@ srn_status srn_create(const srn_config* cfg, const srn_tensors* t, void* workspa
   h->max_points = max_points;
   h->wl = wl;
   h->num_sms = sms;
+  if (cfg->precision == SRN_BF16) {
+    e = cudaStreamCreateWithFlags(&h->side.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      srn_destroy(h);
+      return cuda_fail(e, "side stream");
+    }
+  }
   *out = h;
   return SRN_OK;
 }
@@ -457,6 +469,9 @@ srn_status srn_destroy(srn_handle* h) {
     cudaEventDestroy(h->ev_start[i]);
     cudaEventDestroy(h->ev_stop[i]);
   }
+  if (h->side.fork) cudaEventDestroy(h->side.fork);
+  if (h->side.join) cudaEventDestroy(h->side.join);
+  if (h->side.stream) cudaStreamDestroy(h->side.stream);
   delete h;
   return SRN_OK;
 }
