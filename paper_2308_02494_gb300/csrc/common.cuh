@@ -173,6 +173,31 @@ __device__ __forceinline__ float flat_top(float ux, float uy, float uz, int p,
   return e;
 }
 
+// ------------------------------------------------------------------ packed float pairs
+// Two float32 values in one 64-bit register pair, for the f32x2 arithmetic of sm_100+
+// (one instruction issues both lanes' operation).
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+  return (f2_t)__float_as_uint(lo) | ((f2_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2_lo(f2_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_hi(f2_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // 3x3 determinant of the left block of a 3x4 row-major transform.
 __device__ __forceinline__ float det3(const float* g) {
   return g[0] * (g[5] * g[10] - g[6] * g[9]) - g[1] * (g[4] * g[10] - g[6] * g[8]) +

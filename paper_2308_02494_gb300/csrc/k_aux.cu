@@ -107,14 +107,17 @@ __global__ void __launch_bounds__(ST) k_density_scalar(Bricks br, TrainWs ws, fl
 constexpr int DT = 128;   // points per tile
 constexpr int DNT = 256;  // threads
 
-static_assert(sizeof(TileMap) + DT * (sizeof(float4) + sizeof(float)) + kMaxGrids * 12 * sizeof(float) +
+static_assert(sizeof(TileMap) + DT * 2 * sizeof(float4) + kMaxGrids * 12 * sizeof(float) +
                   DNT * sizeof(double) + 1024 <= kDensityCtaSmem,
               "k_density_grad's shared memory must fit beside the scatter");
+// P10: the paper's p = 10 at compile time, with the x and y axes of the map, the flat
+// top and the sums carried as packed float pairs (the same arithmetic, fewer issued
+// instructions); otherwise one lane per value for any p.
+template <bool P10>
 __global__ void __launch_bounds__(DNT, 4)
 k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, float eps) {
   __shared__ TileMap tm;
-  __shared__ float4 sx[DT];
-  __shared__ float sq[DT];
+  __shared__ float4 sx[DT][2];   // (x, x, y, y), (z, z, q, 0): the pairs the packed path multiplies by
   __shared__ float sg[kMaxGrids * 12];
   __shared__ double red[DNT];
   const int tid = threadIdx.x, M = md.M;
@@ -125,14 +128,16 @@ k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, f
   const int total = tm.first[br.n];
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int tb = blockIdx.x * per, te = min(total, tb + per);
-  float acc[13];
-#pragma unroll
-  for (int j = 0; j < 13; ++j) acc[j] = 0.f;
+  // the 13 sums: sum qE; sum qE e_d (d = x, y, z); sum qE e_d x_e (d major)
+  float s0 = 0.f, s3 = 0.f, s10 = 0.f, s11 = 0.f, s12 = 0.f;
+  f2_t s12p = 0ull, s47 = 0ull, s58 = 0ull, s69 = 0ull;   // (s1, s2), (s4, s7), (s5, s8), (s6, s9)
 
   auto flush = [&](int b) {
+    const float v[13] = {s0, f2_lo(s12p), f2_hi(s12p), s3, f2_lo(s47), f2_lo(s58), f2_lo(s69),
+                         f2_hi(s47), f2_hi(s58), f2_hi(s69), s10, s11, s12};
+#pragma unroll
     for (int j = 0; j < 13; ++j) {
-      red[tid] = (double)acc[j];
-      acc[j] = 0.f;
+      red[tid] = (double)v[j];
       __syncthreads();
       if (pg == 0) {
         double s = 0.0;
@@ -141,10 +146,14 @@ k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, f
       }
       __syncthreads();
     }
+    s0 = s3 = s10 = s11 = s12 = 0.f;
+    s12p = s47 = s58 = s69 = 0ull;
   };
 
   int cur = -1;
   float invS = 0.f, hbar = 0.f, c = 0.f, n = 1.f;
+  f2_t gax = 0ull, gay = 0ull, gaz = 0ull, gt = 0ull;   // rows 0 and 1 of the map, by column
+  float g8 = 0.f, g9 = 0.f, g10 = 0.f, g11 = 0.f;       // row 2
   for (int tile = tb; tile < te; ++tile) {
     const int b = brick_of_tile(tm, br.n, tile, cur);
     if (b != cur) {
@@ -157,37 +166,79 @@ k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, f
       hbar = (float)(ws.acc[b * kAccPerBrick + ACC_SUM_R2] / nb);
       c = (float)ws.acc[b * kAccPerBrick + ACC_C];
       __syncthreads();
+      const float* g = sg + 12 * gi;
+      gax = f2_pack(g[0], g[4]); gay = f2_pack(g[1], g[5]); gaz = f2_pack(g[2], g[6]); gt = f2_pack(g[3], g[7]);
+      g8 = g[8]; g9 = g[9]; g10 = g[10]; g11 = g[11];
     }
     const int64_t p0 = br.off[b] + (int64_t)(tile - tm.first[b]) * DT;
     const int np = (ws.sched && !ws.sched[b].den_on) ? 0 : (int)min((int64_t)DT, br.off[b + 1] - p0);
     if (tid < DT) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      float q = 0.f;
+      float x = 0.f, y = 0.f, z = 0.f, q = 0.f;
       if (tid < np) {
         const int64_t gp = p0 + tid;
-        v = make_float4(xyz[3 * gp], xyz[3 * gp + 1], xyz[3 * gp + 2], 0.f);
+        x = xyz[3 * gp]; y = xyz[3 * gp + 1]; z = xyz[3 * gp + 2];
         const PointDensity d = point_density(ws.rho[gp], ws.herr[gp], invS, hbar, eps, n);
         q = (d.g - c) * invS;
       }
-      sx[tid] = v;
-      sq[tid] = q;
+      sx[tid][0] = make_float4(x, x, y, y);
+      sx[tid][1] = make_float4(z, z, q, 0.f);
     }
     __syncthreads();
-    const float* gg = sg + 12 * gi;
+    if constexpr (P10) {
 #pragma unroll 4
-    for (int p = pg; p < np; p += npg) {
-      const float4 x = sx[p];
-      float ux, uy, uz, ex, ey, ez;
-      affine(gg, x.x, x.y, x.z, ux, uy, uz);
-      const float E = flat_top(ux, uy, uz, md.p, &ex, &ey, &ez);
-      const float w = sq[p] * E;
-      if (w == 0.f) continue;
-      const float wx = w * ex, wy = w * ey, wz = w * ez;
-      acc[0] += w;
-      acc[1] += wx; acc[2] += wy; acc[3] += wz;
-      acc[4] = fmaf(wx, x.x, acc[4]); acc[5] = fmaf(wx, x.y, acc[5]); acc[6] = fmaf(wx, x.z, acc[6]);
-      acc[7] = fmaf(wy, x.x, acc[7]); acc[8] = fmaf(wy, x.y, acc[8]); acc[9] = fmaf(wy, x.z, acc[9]);
-      acc[10] = fmaf(wz, x.x, acc[10]); acc[11] = fmaf(wz, x.y, acc[11]); acc[12] = fmaf(wz, x.z, acc[12]);
+      for (int p = pg; p < np; p += npg) {
+        const float4 xa = sx[p][0], xb = sx[p][1];
+        const f2_t xx = f2_pack(xa.x, xa.y), yy = f2_pack(xa.z, xa.w), zz = f2_pack(xb.x, xb.y);
+        const float x = xa.x, y = xa.z, z = xb.x, q = xb.z;
+        // Eq. 1 (rows 0 and 1 packed, row 2 alone) and exp(-sum_d u_d^20) with 20 u_d^19
+        const f2_t uxy = f2_fma(gax, xx, f2_fma(gay, yy, f2_fma(gaz, zz, gt)));
+        const float uz = fmaf(g8, x, fmaf(g9, y, fmaf(g10, z, g11)));
+        const f2_t s2 = f2_mul(uxy, uxy);
+        f2_t t = f2_mul(s2, s2);
+        t = f2_mul(t, t);
+        t = f2_mul(t, t);
+        const f2_t p18 = f2_mul(t, s2);   // (u_x^18, u_y^18)
+        const float z2 = uz * uz;
+        float pz = z2 * z2;
+        pz = pz * pz;
+        pz = pz * pz;
+        pz = pz * z2;
+        const f2_t p20 = f2_mul(p18, s2);
+        const float ssum = fmaf(pz, z2, f2_lo(p20) + f2_hi(p20));
+        if (!(ssum <= 87.f)) continue;   // exp underflows in float32: no contribution
+        const float w = q * __expf(-ssum);
+        if (w == 0.f) continue;
+        const float w20 = 20.f * w;
+        const f2_t wxy = f2_mul(f2_pack(w20, w20), f2_mul(p18, uxy));   // (w e_x, w e_y)
+        const float wz = w20 * pz * uz;
+        s0 += w;
+        s12p = f2_add(s12p, wxy);
+        s3 += wz;
+        s47 = f2_fma(wxy, xx, s47);
+        s58 = f2_fma(wxy, yy, s58);
+        s69 = f2_fma(wxy, zz, s69);
+        s10 = fmaf(wz, x, s10); s11 = fmaf(wz, y, s11); s12 = fmaf(wz, z, s12);
+      }
+    } else {
+      const float* gg = sg + 12 * gi;
+#pragma unroll 4
+      for (int p = pg; p < np; p += npg) {
+        const float4 xa = sx[p][0], xb = sx[p][1];
+        const float x = xa.x, y = xa.z, z = xb.x;
+        float ux, uy, uz, ex, ey, ez;
+        affine(gg, x, y, z, ux, uy, uz);
+        const float E = flat_top(ux, uy, uz, md.p, &ex, &ey, &ez);
+        const float w = xb.z * E;
+        if (w == 0.f) continue;
+        const float wx = w * ex, wy = w * ey, wz = w * ez;
+        s0 += w;
+        s12p = f2_pack(f2_lo(s12p) + wx, f2_hi(s12p) + wy);
+        s3 += wz;
+        s47 = f2_pack(fmaf(wx, x, f2_lo(s47)), fmaf(wy, x, f2_hi(s47)));
+        s58 = f2_pack(fmaf(wx, y, f2_lo(s58)), fmaf(wy, y, f2_hi(s58)));
+        s69 = f2_pack(fmaf(wx, z, f2_lo(s69)), fmaf(wy, z, f2_hi(s69)));
+        s10 = fmaf(wz, x, s10); s11 = fmaf(wz, y, s11); s12 = fmaf(wz, z, s12);
+      }
     }
     __syncthreads();
   }
@@ -494,7 +545,8 @@ cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, c
   int tiles = 0;
   for (int b = 0; b < br.n; ++b) tiles += (int)((br.off[b + 1] - br.off[b] + DT - 1) / DT);
   const int grid = tiles < ctas_per_sm * L.num_sms ? tiles : ctas_per_sm * L.num_sms;   // 8 warps each
-  k_density_grad<<<grid, DNT, 0, L.stream>>>(md, br, ws, xyz, eps);
+  if (md.p == 10) k_density_grad<true><<<grid, DNT, 0, L.stream>>>(md, br, ws, xyz, eps);
+  else k_density_grad<false><<<grid, DNT, 0, L.stream>>>(md, br, ws, xyz, eps);
   return cudaGetLastError();
 }
 
