@@ -461,26 +461,46 @@ __global__ void k_sample_gen(Bricks br, unsigned long long seed, unsigned long l
   }
 }
 
-// Exclusive scan of one brick's kSortBins counters (one block of 1024 threads per brick).
+// Exclusive scan of one brick's kSortBins counters (one block of 1024 threads per brick):
+// each thread scans 32 consecutive counters (vector loads), the warps scan their threads'
+// totals with shuffles, and one warp scans the 32 warp totals.
 __global__ void __launch_bounds__(1024) k_sample_scan(uint32_t* hist) {
-  __shared__ uint32_t part[1024];
   constexpr int per = kSortBins / 1024;
-  uint32_t* h = hist + (int64_t)blockIdx.x * kSortBins + threadIdx.x * per;
-  uint32_t loc[per];
+  static_assert(per % 4 == 0, "vector loads of the counters");
+  __shared__ uint32_t wsum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint4* h = reinterpret_cast<uint4*>(hist + (int64_t)blockIdx.x * kSortBins + threadIdx.x * per);
+  uint4 v[per / 4];
   uint32_t s = 0;
 #pragma unroll
-  for (int k = 0; k < per; ++k) { loc[k] = s; s += h[k]; }
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {   // Hillis-Steele inclusive scan
-    const uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  for (int k = 0; k < per / 4; ++k) {   // exclusive prefix within the thread
+    v[k] = h[k];
+    const uint32_t a = v[k].x, b = v[k].y, c = v[k].z, d = v[k].w;
+    v[k] = make_uint4(s, s + a, s + a + b, s + a + b + c);
+    s += a + b + c + d;
   }
-  const uint32_t base = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  uint32_t incl = s;   // inclusive scan of the thread totals within the warp
 #pragma unroll
-  for (int k = 0; k < per; ++k) h[k] = base + loc[k];
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = wsum[lane], wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    wsum[lane] = wi - w;   // exclusive
+  }
+  __syncthreads();
+  const uint32_t base = wsum[warp] + incl - s;
+#pragma unroll
+  for (int k = 0; k < per / 4; ++k)
+    h[k] = make_uint4(base + v[k].x, base + v[k].y, base + v[k].z, base + v[k].w);
 }
 
 __global__ void k_sample_scatter(Bricks br, const float* __restrict__ tmp, const uint32_t* __restrict__ rank,

@@ -718,9 +718,11 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
           // Eq. 2's set-up as make_cell computes it; for points inside the grid s lies in
           // [0, R-1] already (the rounding of fmaf is monotone), so no clamp is needed
           if (!((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f))) continue;
+          // (cell floor(s): it differs from min(floor(s), R-2) only at s = R-1, whose cell
+          // R-1 is never in a box and takes the exact path below)
           Cell c;
           const float sx = fmaf(ux, hs, hs), sy = fmaf(uy, hs, hs), sz = fmaf(uz, hs, hs);
-          c.cx = min((int)sx, R - 2); c.cy = min((int)sy, R - 2); c.cz = min((int)sz, R - 2);
+          c.cx = (int)sx; c.cy = (int)sy; c.cz = (int)sz;
           c.wx = sx - (float)c.cx; c.wy = sy - (float)c.cy; c.wz = sz - (float)c.cz;
           c.inside = true;
           const float g0 = __uint_as_float(d << 16), g1 = __uint_as_float(d & 0xffff0000u);
@@ -735,7 +737,7 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
             red_pair<C>(a0 + oz, zy2 * ax, zy2 * c.wx, gs0, gs1);
             red_pair<C>(a0 + oy + oz, zy3 * ax, zy3 * c.wx, gs0, gs1);
           } else {   // outside the tile's box (rounding at its faces, or an unsorted batch)
-            scatter_point(dFi, c, R, C, g0, C == 2 ? g1 : 0.f);
+            scatter_point(dFi, make_cell(ux, uy, uz, R), R, C, g0, C == 2 ? g1 : 0.f);
           }
         }
       }
@@ -951,7 +953,22 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn)
       float ux, uy, uz;
       affine(gi, x.x, x.y, x.z, ux, uy, uz);
       if constexpr (DENS) {   // det E 2^S as an integer; the warp's (group's) sum into the point's slot
-        const float t = valid ? flat_top(ux, uy, uz, P10 ? 10 : md.p) : 0.f;
+        float t;
+        if constexpr (P10) {   // exp(-sum_d u_d^20), the x and y axes as a packed pair
+          const f2_t uxy = f2_pack(ux, uy), s2 = f2_mul(uxy, uxy);
+          f2_t q = f2_mul(s2, s2);
+          q = f2_mul(q, q);
+          q = f2_mul(q, q);
+          const f2_t p20 = f2_mul(f2_mul(q, s2), s2);
+          const float z2 = uz * uz;
+          float pz = z2 * z2;
+          pz = pz * pz;
+          pz = pz * pz;
+          const float ssum = fmaf(pz * z2, z2, f2_lo(p20) + f2_hi(p20));
+          t = valid && ssum <= 87.f ? __expf(-ssum) : 0.f;
+        } else {
+          t = valid ? flat_top(ux, uy, uz, md.p) : 0.f;
+        }
         int32_t v = __float_as_int(fmaf(t, dq, kMagic)) - kMagicBits;
         if (M >= 32) {
           v = __reduce_add_sync(0xffffffffu, v);
@@ -964,10 +981,12 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn)
       if (!valid) continue;
       uint32_t yv = 0u;
       if ((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f)) {
-        // Eq. 2's set-up as make_cell computes it (no clamp needed inside the grid)
+        // Eq. 2's set-up as make_cell computes it: inside the grid s lies in [0, R-1] (the
+        // rounding of fmaf is monotone); the cell min(floor(s), R-2) differs from floor(s)
+        // only at s = R-1, whose cell R-1 is never in a box and takes the exact path below
         Cell c;
         const float sx = fmaf(ux, hs, hs), sy = fmaf(uy, hs, hs), sz = fmaf(uz, hs, hs);
-        c.cx = min((int)sx, R - 2); c.cy = min((int)sy, R - 2); c.cz = min((int)sz, R - 2);
+        c.cx = (int)sx; c.cy = (int)sy; c.cz = (int)sz;
         c.wx = sx - (float)c.cx; c.wy = sy - (float)c.cy; c.wz = sz - (float)c.cz;
         c.inside = true;
         const unsigned lx = (unsigned)(c.cx - lox), ly = (unsigned)(c.cy - loy), lz = (unsigned)(c.cz - loz);
@@ -994,7 +1013,7 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn)
             yv = __bfloat16_as_ushort(__float2bfloat16_rn(fmaf(c.wz, f23 - f01, f01)));
           }
         } else {   // outside the tile's box: the corners from global memory
-          yv = enc_global<C>(Fi, c, R);
+          yv = enc_global<C>(Fi, make_cell(ux, uy, uz, R), R);
         }
       }
       Yt[p * M] = (E)yv;
