@@ -552,6 +552,13 @@ int blocks_for(int64_t n, int threads, int num_sms, int per_sm) {
 
 }  // namespace
 
+int density_grad_cta_regs(int p) {
+  cudaFuncAttributes a;
+  const void* k = p == 10 ? (const void*)k_density_grad<true> : (const void*)k_density_grad<false>;
+  if (cudaFuncGetAttributes(&a, k) != cudaSuccess) return 0;
+  return ((a.numRegs + 7) / 8) * 8 * DNT;   // registers are granted per warp in steps of 8 per thread
+}
+
 cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, const TrainWs& ws,
                            const float* xyz, float eps, int ctas_per_sm) {
   const int64_t total = br.off[br.n];

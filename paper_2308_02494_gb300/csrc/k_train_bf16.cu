@@ -1231,9 +1231,22 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     mark_stop(1);
   }
   if (dens && side) {   // the density passes beside the scatter
+    // one CTA per SM when it fits beside the scatter's CTA (registers; shared memory is
+    // reserved by scat_capn), else the usual four, which then mostly follow the scatter
+    int ctas = 4;
+    {
+      cudaFuncAttributes fa;
+      int dev = 0, regs_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+      const int dregs = density_grad_cta_regs(md.p);
+      if (dregs > 0 && cudaFuncGetAttributes(&fa, md.C == 2 ? (const void*)k_scat<2> : (const void*)k_scat<1>) == cudaSuccess &&
+          ((fa.numRegs + 7) / 8) * 8 * SNT + dregs <= regs_sm)
+        ctas = 1;
+    }
     if ((e = cudaEventRecord(side->fork, L.stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(side->stream, side->fork, 0)) != cudaSuccess) return e;
-    if ((e = launch_density(Launch{side->stream, L.num_sms}, md, br, ws, xyz, ws.eps, 1)) != cudaSuccess) return e;
+    if ((e = launch_density(Launch{side->stream, L.num_sms}, md, br, ws, xyz, ws.eps, ctas)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(side->join, side->stream)) != cudaSuccess) return e;
   }
   {
