@@ -120,14 +120,13 @@ k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, f
   __shared__ float4 sx[DT][2];   // (x, x, y, y), (z, z, q, 0): the pairs the packed path multiplies by
   __shared__ float sg[kMaxGrids * 12];
   __shared__ double red[DNT];
+  __shared__ int s_tile;
   const int tid = threadIdx.x, M = md.M;
   const int npg = DNT / M;             // point groups (M divides 256)
   const int gi = tid % M, pg = tid / M;
   if (tid == 0) build_tile_map(br, DT, tm);
   __syncthreads();
   const int total = tm.first[br.n];
-  const int per = (total + gridDim.x - 1) / gridDim.x;
-  const int tb = blockIdx.x * per, te = min(total, tb + per);
   // the 13 sums: sum qE; sum qE e_d (d = x, y, z); sum qE e_d x_e (d major)
   float s0 = 0.f, s3 = 0.f, s10 = 0.f, s11 = 0.f, s12 = 0.f;
   f2_t s12p = 0ull, s47 = 0ull, s58 = 0ull, s69 = 0ull;   // (s1, s2), (s4, s7), (s5, s8), (s6, s9)
@@ -154,7 +153,13 @@ k_density_grad(Model md, Bricks br, TrainWs ws, const float* __restrict__ xyz, f
   float invS = 0.f, hbar = 0.f, c = 0.f, n = 1.f;
   f2_t gax = 0ull, gay = 0ull, gaz = 0ull, gt = 0ull;   // rows 0 and 1 of the map, by column
   float g8 = 0.f, g9 = 0.f, g10 = 0.f, g11 = 0.f;       // row 2
-  for (int tile = tb; tile < te; ++tile) {
+  // tiles are taken from a counter (in increasing order per CTA), so CTAs that start
+  // late -- beside or after the scatter -- share the remaining work
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(ws.tile_ctr + 3, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= total) break;
     const int b = brick_of_tile(tm, br.n, tile, cur);
     if (b != cur) {
       if (cur >= 0) flush(cur);
@@ -552,13 +557,6 @@ int blocks_for(int64_t n, int threads, int num_sms, int per_sm) {
 
 }  // namespace
 
-int density_grad_cta_regs(int p) {
-  cudaFuncAttributes a;
-  const void* k = p == 10 ? (const void*)k_density_grad<true> : (const void*)k_density_grad<false>;
-  if (cudaFuncGetAttributes(&a, k) != cudaSuccess) return 0;
-  return ((a.numRegs + 7) / 8) * 8 * DNT;   // registers are granted per warp in steps of 8 per thread
-}
-
 cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, const TrainWs& ws,
                            const float* xyz, float eps, int ctas_per_sm) {
   const int64_t total = br.off[br.n];
@@ -572,6 +570,7 @@ cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, c
   int tiles = 0;
   for (int b = 0; b < br.n; ++b) tiles += (int)((br.off[b + 1] - br.off[b] + DT - 1) / DT);
   const int grid = tiles < ctas_per_sm * L.num_sms ? tiles : ctas_per_sm * L.num_sms;   // 8 warps each
+  if ((e = cudaMemsetAsync(ws.tile_ctr + 3, 0, sizeof(int32_t), L.stream)) != cudaSuccess) return e;
   if (md.p == 10) k_density_grad<true><<<grid, DNT, 0, L.stream>>>(md, br, ws, xyz, eps);
   else k_density_grad<false><<<grid, DNT, 0, L.stream>>>(md, br, ws, xyz, eps);
   return cudaGetLastError();

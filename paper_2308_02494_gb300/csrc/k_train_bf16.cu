@@ -370,7 +370,7 @@ struct ScatHead {
   float4 xs[ST];               // the tile's points
   uint2 box[kMaxGrids];        // node box of the tile's block per grid: lo | nodes per axis (bytes)
   uint32_t gmax[kMaxGrids];    // largest |dL/dy| of the tile per grid (bf16 bits)
-  ScatTile tile;
+  ScatTile tile, tnext;         // this tile, and the next one (taken one ahead)
 };
 
 // Thread -> grid, column group and point group of k_scat.  With M >= 32 the lanes of a
@@ -603,8 +603,10 @@ __device__ uint2 tile_box(uint32_t code, const float* __restrict__ g, int R) {
   return make_uint2(blo, bn);
 }
 
+// At most 96 registers: with them a CTA of the density pass (8 warps x 64) fits beside
+// the scatter's 16 warps in one SM's register file.
 template <int C>
-__global__ void __launch_bounds__(SNT, 1)
+__global__ void __maxnreg__(96)
 k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn) {
   extern __shared__ __align__(16) unsigned char smraw[];
   ScatHead& h = *reinterpret_cast<ScatHead*>(smraw);
@@ -626,16 +628,30 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
   int32_t* col = acc + mp.grp * capn * kNode + lane;         // this thread's column
   const uint32_t col_s = su32(col);
   constexpr uint32_t kNz = C == 2 ? 0x7fff7fffu : 0x7fffu;    // nonzero dL/dy
+  bool first = true;
   for (;;) {
     // tiles are taken in list order (brick by brick, Morton order inside a brick), so
-    // the CTAs on the GPU at one time work on neighbouring blocks of one brick
+    // the CTAs on the GPU at one time work on neighbouring blocks of one brick; each CTA
+    // takes its next tile one ahead and asks L2 for that tile's dL/dy rows (contiguous)
     if (tid == 0) {
-      const int t = atomicAdd(ws.tile_ctr + 1, 1);
-      ScatTile T;
-      T.start = 0; T.count = -1; T.code = 0;
-      if (t < ntiles) T = ws.tiles[t];
-      h.tile = T;
+      auto take = [&]() {
+        const int t = atomicAdd(ws.tile_ctr + 1, 1);
+        ScatTile T;
+        T.start = 0; T.count = -1; T.code = 0;
+        if (t < ntiles) T = ws.tiles[t];
+        return T;
+      };
+      h.tile = first ? take() : h.tnext;
+      h.tnext = h.tile.count < 0 ? h.tile : take();
+      if (h.tnext.count > 0) {
+        const char* rows = reinterpret_cast<const char*>(ws.dY + h.tnext.start * md.K);
+        const uint32_t bytes = (uint32_t)h.tnext.count * (uint32_t)md.K * 2u;   // a multiple of 16
+        for (uint32_t o = 0; o < bytes; o += 65536u)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(rows + o), "r"(min(65536u, bytes - o))
+                       : "memory");
+      }
     }
+    first = false;
     __syncthreads();   // also: the previous tile's flush has finished with h
     const ScatTile T = h.tile;
     if (T.count < 0) break;
@@ -657,7 +673,8 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
     // the block's boxes bound the points only if all of them lie in the block (always,
     // for a Morton-sorted batch); otherwise points outside a box add their corners directly
     const bool in_block = __syncthreads_and(mine_in) != 0;
-    {  // largest |dL/dy| of every grid over the tile (eight loads in flight)
+    {  // largest |dL/dy| of every grid over the tile (eight loads in flight; the rows were
+       // prefetched into L2 while the previous tile ran)
       uint32_t mx = 0u;
       for (int p = mp.pg; p < np; p += 8 * mp.npg) {
         uint32_t d[8];
@@ -1231,19 +1248,10 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     mark_stop(1);
   }
   if (dens && side) {   // the density passes beside the scatter
-    // one CTA per SM when it fits beside the scatter's CTA (registers; shared memory is
-    // reserved by scat_capn), else the usual four, which then mostly follow the scatter
-    int ctas = 4;
-    {
-      cudaFuncAttributes fa;
-      int dev = 0, regs_sm = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-      const int dregs = density_grad_cta_regs(md.p);
-      if (dregs > 0 && cudaFuncGetAttributes(&fa, md.C == 2 ? (const void*)k_scat<2> : (const void*)k_scat<1>) == cudaSuccess &&
-          ((fa.numRegs + 7) / 8) * 8 * SNT + dregs <= regs_sm)
-        ctas = 1;
-    }
+    // four CTAs per SM taking tiles from a counter: one fits beside the scatter's CTA
+    // (registers and the shared memory scat_capn leaves), the others start as the
+    // scatter's CTAs finish
+    const int ctas = 4;
     if ((e = cudaEventRecord(side->fork, L.stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(side->stream, side->fork, 0)) != cudaSuccess) return e;
     if ((e = launch_density(Launch{side->stream, L.num_sms}, md, br, ws, xyz, ws.eps, ctas)) != cudaSuccess) return e;

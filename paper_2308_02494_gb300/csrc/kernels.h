@@ -47,9 +47,6 @@ cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, c
                            const float* xyz, float eps, int ctas_per_sm = 4);
 // Shared memory a CTA of the third density pass needs on its SM (static + reserved).
 constexpr int kDensityCtaSmem = 16 * 1024;
-// Registers of one CTA of the third density pass (for the flat-top exponent p), or 0 if
-// the attributes cannot be read.
-int density_grad_cta_regs(int p);
 cudaError_t launch_finalize(const Launch& L, const Bricks& br, const Model& md, const TrainWs& ws,
                             bool density, float* dG, int64_t sdG, double* losses);
 
