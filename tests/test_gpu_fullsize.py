@@ -76,3 +76,46 @@ def test_eight_brick_forward_sampled(precision):
         got = f[off[b]:off[b + 1]][pick][keep]
         # forward values are continuous in the operand rounding, so no kink filter is needed
         assert rel_l2(got, want) <= TOL[precision], (b, rel_l2(got, want))
+
+
+def test_eight_brick_training_pass_gradients():
+    """The benchmark's BF16 training pass as it runs there (8 uneven bricks, 2 653 469
+    points, the density passes on the second stream beside the scatter): losses and every
+    gradient of the two smallest bricks (81 524 and 131 669 points) against the oracle.
+    Those bricks' points are kept off grid faces and ReLU kinks; the other bricks'
+    points are the sampler's as they come."""
+    import torch
+    counts = synth.uneven_counts(8, 1 << 16, 1 << 19, seed=1)
+    check = [int(b) for b in np.argsort(counts)[:2]]
+    m, refs = make_model(SHAPE, 8, "bf16", int(counts.sum()), seed=43, shrink=0.3)
+    r = np.random.default_rng(17)
+    xs, vs = [], []
+    for b, c in enumerate(counts):
+        c = int(c)
+        if b in check:
+            x = osp.sample_points(11, 0, b, c + c // 2)
+            u = ap.local_coords(refs[b]["G"], x.astype(np.float64))
+            x = points_off_kinks(refs[b], x[np.all(np.abs(np.abs(u) - 1.0) > 1e-5, axis=(1, 2))], RND["bf16"])
+            assert len(x) >= c
+            x = x[:c]
+        else:
+            x = osp.sample_points(11, 0, b, c)
+        xs.append(morton_sorted(x))
+        vs.append(r.uniform(-0.5, 1.5, c).astype(np.float32))
+    off = m.offsets_of(counts)
+    losses = m.backward(torch.as_tensor(np.concatenate(xs), device="cuda"),
+                        torch.as_tensor(np.concatenate(vs), device="cuda"), off, density=True).cpu().numpy()
+    grads = m.get("grads")
+    tol = TOL["bf16"]
+    for b in check:
+        x = xs[b].astype(np.float64)
+        o = ap.grad_rec(refs[b], x, vs[b].astype(np.float64), rnd=RND["bf16"])
+        d = ap.grad_density(refs[b]["G"], x, o["h"])
+        assert losses[b, 3] == counts[b]
+        assert abs(losses[b, 0] - o["L_rec"]) <= tol * o["L_rec"], b
+        assert abs(losses[b, 1] - d["L_den"]) <= tol * abs(d["L_den"]), b
+        g = grads[b]
+        errs = {k: rel_l2(g[k], want) for k, want in (("F", o["dF"]), ("W1", o["dW1"]), ("W2", o["dW2"]),
+                                                      ("w3", o["dw3"]))}
+        errs["G"] = dG_error(g["G"], d["dG"], density_grad_scale(refs[b]["G"], x, o["h"]))
+        assert all(e <= tol for e in errs.values()), (b, errs)
