@@ -28,6 +28,100 @@ __device__ __forceinline__ Tv warp_sum(Tv v) {
   return v;
 }
 
+// ------------------------------------------------------------ density pass 1
+// rho(x) = sum_i det(A_i) exp(-sum_d u_d^2p) (Eq. 7) per point and its sum S per brick,
+// one thread per point over the grids; for the BF16 training pass, which runs it on the
+// second stream beside the decoder (it needs only the points and the transforms).
+// Tiles of RHP points come from a counter; the float32 terms of a point are summed in
+// float32, the points of a brick in float64.
+constexpr int RHT = 256;   // threads; one CTA fits beside two decoder CTAs (at most 56 registers)
+constexpr int RHP = 2 * RHT;   // points per tile: two per thread, interleaved for latency
+
+// exp(-sum_d u_d^2p) of Eq. 7 for p = 10 (x and y axes as a packed pair) or any p
+template <bool P10>
+__device__ __forceinline__ float flat_top_value(float ux, float uy, float uz, int p) {
+  if constexpr (P10) {
+    const f2_t uxy = f2_pack(ux, uy), s2 = f2_mul(uxy, uxy);
+    f2_t q = f2_mul(s2, s2);
+    q = f2_mul(q, q);
+    q = f2_mul(q, q);
+    const f2_t p20 = f2_mul(f2_mul(q, s2), s2);
+    const float z2 = uz * uz;
+    float pz = z2 * z2;
+    pz = pz * pz;
+    pz = pz * pz;
+    const float ssum = fmaf(pz * z2, z2, f2_lo(p20) + f2_hi(p20));
+    return ssum <= 87.f ? __expf(-ssum) : 0.f;
+  } else {
+    return flat_top(ux, uy, uz, p);
+  }
+}
+
+template <bool P10>
+__global__ void __maxnreg__(56)
+k_density_rho(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
+  __shared__ Bricks br;
+  __shared__ TileMap tm;
+  __shared__ __align__(16) float sg[kMaxGrids * 12];
+  __shared__ float sdet[kMaxGrids];
+  __shared__ double red[RHT / 32];
+  __shared__ int s_tile;
+  load_bricks(brp, br);
+  const int tid = threadIdx.x, lane = tid & 31, M = md.M;
+  if (tid == 0) build_tile_map(br, RHP, tm);
+  __syncthreads();
+  const int total = tm.first[br.n];
+  double sum = 0.0;
+  int cur = -1;
+  auto flush = [&](int b) {   // block-uniform
+    const double w = warp_sum(sum);
+    if (lane == 0) red[tid >> 5] = w;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int q = 0; q < RHT / 32; ++q) t += red[q];
+      atomicAdd(ws.acc + b * kAccPerBrick + ACC_SUM_RHO, t);
+    }
+    sum = 0.0;
+  };
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(ws.tile_ctr + 4, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= total) break;
+    const int b = brick_of_tile(tm, br.n, tile, cur);
+    if (b != cur) {
+      if (cur >= 0) flush(cur);
+      cur = b;
+      const float* G = md.G + (int64_t)b * md.sG;
+      for (int k = tid; k < M * 12; k += RHT) sg[k] = G[k];
+      for (int i = tid; i < M; i += RHT) sdet[i] = det3(G + 12 * i);
+      __syncthreads();
+    }
+    const int64_t pa = br.off[b] + (int64_t)(tile - tm.first[b]) * RHP + tid, pb = pa + RHT;
+    const bool va = pa < br.off[b + 1], vb = pb < br.off[b + 1];
+    const float xa = va ? xyz[3 * pa] : 0.f, ya = va ? xyz[3 * pa + 1] : 0.f, za = va ? xyz[3 * pa + 2] : 0.f;
+    const float xb = vb ? xyz[3 * pb] : 0.f, yb = vb ? xyz[3 * pb + 1] : 0.f, zb = vb ? xyz[3 * pb + 2] : 0.f;
+    float ra = 0.f, rb = 0.f;
+#pragma unroll 2
+    for (int i = 0; i < M; ++i) {
+      const float4* g4 = reinterpret_cast<const float4*>(sg + 12 * i);
+      const float4 a = g4[0], c = g4[1], d = g4[2];
+      const float det = sdet[i];
+      ra = fmaf(det, flat_top_value<P10>(fmaf(a.x, xa, fmaf(a.y, ya, fmaf(a.z, za, a.w))),
+                                         fmaf(c.x, xa, fmaf(c.y, ya, fmaf(c.z, za, c.w))),
+                                         fmaf(d.x, xa, fmaf(d.y, ya, fmaf(d.z, za, d.w))), md.p), ra);
+      rb = fmaf(det, flat_top_value<P10>(fmaf(a.x, xb, fmaf(a.y, yb, fmaf(a.z, zb, a.w))),
+                                         fmaf(c.x, xb, fmaf(c.y, yb, fmaf(c.z, zb, c.w))),
+                                         fmaf(d.x, xb, fmaf(d.y, yb, fmaf(d.z, zb, d.w))), md.p), rb);
+    }
+    if (va) { ws.rho[pa] = ra; sum += (double)ra; }
+    if (vb) { ws.rho[pb] = rb; sum += (double)rb; }
+    __syncthreads();
+  }
+  if (cur >= 0) flush(cur);
+}
+
 // ------------------------------------------------------------ density pass 2
 // Per point: rho_s = rho/S, k = hbar/(h+eps), rho* = exp(k log(rho_s+eps)) (held
 // constant), g = dL/drho_s = -rho*/(N (rho_s+eps)).  Sums per brick:
@@ -556,6 +650,16 @@ int blocks_for(int64_t n, int threads, int num_sms, int per_sm) {
 }
 
 }  // namespace
+
+cudaError_t launch_density_rho(const Launch& L, const Model& md, const Bricks& br, const TrainWs& ws,
+                               const float* xyz) {
+  if (br.off[br.n] == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(ws.tile_ctr + 4, 0, sizeof(int32_t), L.stream);
+  if (e != cudaSuccess) return e;
+  if (md.p == 10) k_density_rho<true><<<L.num_sms, RHT, 0, L.stream>>>(md, br, ws, xyz);
+  else k_density_rho<false><<<L.num_sms, RHT, 0, L.stream>>>(md, br, ws, xyz);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, const TrainWs& ws,
                            const float* xyz, float eps, int ctas_per_sm) {

@@ -1220,16 +1220,22 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     const int capn = enc_capn(md.M, md.C);
     const size_t smem = enc_smem(md.M, md.C, capn);
     const bool p10 = md.p == 10;
-    const void* kern = md.C == 2 ? (dens ? (p10 ? (const void*)k_enc<2, true, true> : (const void*)k_enc<2, true, false>)
-                                         : (const void*)k_enc<2, false, true>)
-                                 : (dens ? (p10 ? (const void*)k_enc<1, true, true> : (const void*)k_enc<1, true, false>)
-                                         : (const void*)k_enc<1, false, true>);
+    const bool edens = dens && !side;   // with the second stream, rho is its first pass
+    const void* kern = md.C == 2 ? (edens ? (p10 ? (const void*)k_enc<2, true, true> : (const void*)k_enc<2, true, false>)
+                                          : (const void*)k_enc<2, false, true>)
+                                 : (edens ? (p10 ? (const void*)k_enc<1, true, true> : (const void*)k_enc<1, true, false>)
+                                          : (const void*)k_enc<1, false, true>);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
     const int grid = L.num_sms * occupancy(kern, SNT, smem);
     mark_start(0);
     void* args[] = {(void*)&md, (void*)&br, (void*)&ws, (void*)&xyz, (void*)&capn};
     if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(SNT), args, smem, L.stream)) != cudaSuccess) return e;
+    if (dens && side) {   // rho beside the decoder
+      if ((e = cudaEventRecord(side->enc_done, L.stream)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(side->stream, side->enc_done, 0)) != cudaSuccess) return e;
+      if ((e = launch_density_rho(Launch{side->stream, L.num_sms}, md, br, ws, xyz)) != cudaSuccess) return e;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark_stop(0);
   }
@@ -1247,7 +1253,7 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark_stop(1);
   }
-  if (dens && side) {   // the density passes beside the scatter
+  if (dens && side) {   // the other two density passes beside the scatter, after the decoder
     // four CTAs per SM taking tiles from a counter: one fits beside the scatter's CTA
     // (registers and the shared memory scat_capn leaves), the others start as the
     // scatter's CTAs finish

@@ -23,13 +23,13 @@ struct KernelMark {
   int which;
   cudaEvent_t start, stop;
 };
-// A second stream for work that runs beside the scatter: with `dens`, the density
-// passes (which need the decoder's h and the encoder's rho, and nothing of the scatter)
-// run there, forked after the decoder and joined before the pass returns; one CTA per SM
-// of them fits beside the scatter's CTA.
+// A second stream for the density loss beside the main chain: with `dens` its first
+// pass (rho, which needs only the points and the transforms) is forked after the encoder
+// and runs beside the decoder; the other two (which need the decoder's h) wait for the
+// decoder and run beside the scatter; the pass joins before it returns.
 struct SideStream {
   cudaStream_t stream;
-  cudaEvent_t fork, join;
+  cudaEvent_t fork, join, enc_done;
 };
 cudaError_t launch_train_bf16(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
                               const TrainWs& ws, const float* xyz, const float* target,
@@ -45,6 +45,9 @@ cudaError_t launch_query_fp32(const Launch& L, QueryMode mode, const Model& md, 
 // Density loss (Eq. 7-9) second and third passes, and the per-brick finalisation.
 cudaError_t launch_density(const Launch& L, const Model& md, const Bricks& br, const TrainWs& ws,
                            const float* xyz, float eps, int ctas_per_sm = 4);
+// The first pass alone (rho per point and its sum per brick), one CTA per SM.
+cudaError_t launch_density_rho(const Launch& L, const Model& md, const Bricks& br, const TrainWs& ws,
+                               const float* xyz);
 // Shared memory a CTA of the third density pass needs on its SM (static + reserved).
 constexpr int kDensityCtaSmem = 16 * 1024;
 cudaError_t launch_finalize(const Launch& L, const Bricks& br, const Model& md, const TrainWs& ws,

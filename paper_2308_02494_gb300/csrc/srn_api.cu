@@ -167,7 +167,7 @@ struct srn_handle {
   double timed_ms = 0.0;
   int64_t timed_launches = 0;
   // BF16 training: a second stream for the density passes beside the scatter
-  srn::SideStream side{nullptr, nullptr, nullptr};
+  srn::SideStream side{nullptr, nullptr, nullptr, nullptr};
 
   srn::StepState* state() const { return reinterpret_cast<srn::StepState*>(ws + wl.state); }
   srn::BrickSched* sched() const { return reinterpret_cast<srn::BrickSched*>(ws + wl.sched); }
@@ -452,6 +452,7 @@ srn_status srn_create(const srn_config* cfg, const srn_tensors* t, void* workspa
     e = cudaStreamCreateWithFlags(&h->side.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->side.enc_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
       srn_destroy(h);
       return cuda_fail(e, "side stream");
@@ -471,6 +472,7 @@ srn_status srn_destroy(srn_handle* h) {
   }
   if (h->side.fork) cudaEventDestroy(h->side.fork);
   if (h->side.join) cudaEventDestroy(h->side.join);
+  if (h->side.enc_done) cudaEventDestroy(h->side.enc_done);
   if (h->side.stream) cudaStreamDestroy(h->side.stream);
   delete h;
   return SRN_OK;
