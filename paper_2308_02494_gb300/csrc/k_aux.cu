@@ -434,7 +434,8 @@ __device__ __forceinline__ void adam4(float4& P, const float4 G, float4& Mm, flo
 // when the brick's density decision says so, with its own bias corrections.
 __global__ void k_adam(AdamLayout lay, float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, uint16_t* __restrict__ shadow, int do_b, float lr_a, float lr_b,
-                       float b1, float b2, float eps, const StepState* st, const BrickSched* sched, float pfactor) {
+                       float b1, float b2, float eps, const StepState* st, const BrickSched* sched, float pfactor,
+                       int seg0, int seg1) {
   const int b = blockIdx.y;
   float mult = 1.f, bc1b = st->bc1b, rbc2b = st->rbc2b;
   bool den = do_b != 0;
@@ -448,7 +449,7 @@ __global__ void k_adam(AdamLayout lay, float* __restrict__ p, float* __restrict_
   }
   const float bc1a = st->bc1a, rbc2a = st->rbc2a;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int sgm = 0; sgm < 5; ++sgm) {
+  for (int sgm = seg0; sgm < seg1; ++sgm) {
     const bool a = sgm < 4;
     if (!a && !den) break;
     const int64_t base = lay.off[sgm] + (int64_t)b * lay.size[sgm];   // a multiple of 64
@@ -688,15 +689,19 @@ cudaError_t launch_finalize(const Launch& L, const Bricks& br, const Model& md, 
 
 cudaError_t launch_adam(const Launch& L, const AdamLayout& lay, float* p, float* g, float* m, float* v,
                         uint16_t* shadow, bool do_b, float lr_a, float lr_b, float beta1, float beta2, float eps,
-                        StepState* st, const BrickSched* sched, float pfactor) {
-  k_advance<<<1, 1, 0, L.stream>>>(st, do_b ? 1 : 0, beta1, beta2);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int64_t per_brick = (lay.size[0] + lay.size[1] + lay.size[2] + lay.size[3] + lay.size[4]) / 4;
+                        StepState* st, const BrickSched* sched, float pfactor, int seg0, int seg1, bool advance) {
+  cudaError_t e;
+  if (advance) {
+    k_advance<<<1, 1, 0, L.stream>>>(st, do_b ? 1 : 0, beta1, beta2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  int64_t per_brick = 0;
+  for (int k = seg0; k < seg1; ++k) per_brick += lay.size[k] / 4;
+  if (per_brick == 0) return cudaSuccess;
   const int bx = (int)std::max<int64_t>(1, std::min<int64_t>((per_brick + 511) / 512,
                                                              (int64_t)8 * L.num_sms / lay.n_bricks + 1));
   k_adam<<<dim3(bx, lay.n_bricks), 256, 0, L.stream>>>(lay, p, g, m, v, shadow, do_b ? 1 : 0, lr_a, lr_b, beta1,
-                                                       beta2, eps, st, sched, pfactor);
+                                                       beta2, eps, st, sched, pfactor, seg0, seg1);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ struct KernelMark {
 struct SideStream {
   cudaStream_t stream;
   cudaEvent_t fork, join, enc_done;
+  bool defer_join;   // the caller waits for `join` itself (later work can run beside the tail)
 };
 cudaError_t launch_train_bf16(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
                               const TrainWs& ws, const float* xyz, const float* target,
@@ -93,9 +94,12 @@ struct AdamLayout {
   int64_t off[5], size[5];    // segment offsets and per-brick strides (floats)
   int n_bricks;
 };
+// Segments [seg0, seg1) of (F, W1, W2, w3, G); `advance` first advances the step state
+// (once per step, before the first segments).
 cudaError_t launch_adam(const Launch& L, const AdamLayout& lay, float* p, float* g, float* m, float* v,
                         uint16_t* shadow, bool do_b, float lr_a, float lr_b, float beta1, float beta2, float eps,
-                        StepState* st, const BrickSched* sched, float pfactor);
+                        StepState* st, const BrickSched* sched, float pfactor, int seg0 = 0, int seg1 = 5,
+                        bool advance = true);
 cudaError_t launch_shadow(const Launch& L, const float* p, uint16_t* shadow, int64_t n);
 
 // Sampler (Philox + Morton counting sort) and ground-truth lookup.

@@ -167,7 +167,7 @@ struct srn_handle {
   double timed_ms = 0.0;
   int64_t timed_launches = 0;
   // BF16 training: a second stream for the density passes beside the scatter
-  srn::SideStream side{nullptr, nullptr, nullptr, nullptr};
+  srn::SideStream side{nullptr, nullptr, nullptr, nullptr, false};
 
   srn::StepState* state() const { return reinterpret_cast<srn::StepState*>(ws + wl.state); }
   srn::BrickSched* sched() const { return reinterpret_cast<srn::BrickSched*>(ws + wl.sched); }
@@ -304,8 +304,23 @@ srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn
   return SRN_OK;
 }
 
+srn_status do_finalize(srn_handle* h, void* stream, const srn::Bricks& br, uint32_t flags, double* losses) {
+  const srn::BrickSched* sched = (flags & SRN_SCHEDULE) ? h->sched() : nullptr;
+  const bool dens = (flags & SRN_DENSITY) != 0 || sched;
+  srn::TrainWs tws = h->train_ws();
+  tws.sched = sched;
+  tws.rec_dg = (flags & SRN_REC_DG) ? 1 : 0;
+  cudaError_t e = srn::launch_finalize(h->launch(stream), br, h->model(), tws, dens, h->t.grads_dev + h->lay.off_G,
+                                       h->lay.size_G, losses);
+  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
+  return SRN_OK;
+}
+
+// With `split` (the BF16 pass with its density passes on the second stream) the pass
+// returns before the finalisation and without waiting for the second stream: the caller
+// waits for h->side.join and calls do_finalize.
 srn_status do_backward(srn_handle* h, void* stream, const float* xyz, const float* target,
-                       const srn::Bricks& br, uint32_t flags, double* losses) {
+                       const srn::Bricks& br, uint32_t flags, double* losses, bool split = false) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // with the training routine, the density passes always run and each brick follows
   // its device-side decision
@@ -316,9 +331,11 @@ srn_status do_backward(srn_handle* h, void* stream, const float* xyz, const floa
     e = cudaMemsetAsync(h->ws + h->wl.acc, 0, h->wl.rsum - h->wl.acc + sizeof(double) * 12 * h->cfg.n_grids * h->cfg.n_bricks, s);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   const int rec_dg = (flags & SRN_REC_DG) ? 1 : 0;
+  h->side.defer_join = split;
   srn_status st = run_query(h, stream, dens ? srn::kTrainDensity : srn::kTrain, br, xyz, target,
                             nullptr, (flags & SRN_UPSTREAM) ? 1 : 0, sched, rec_dg);
-  if (st != SRN_OK) return st;
+  h->side.defer_join = false;
+  if (st != SRN_OK || split) return st;
   const srn::Launch L = h->launch(stream);
   const srn::Model md = h->model();
   srn::TrainWs tws = h->train_ws();
@@ -328,13 +345,10 @@ srn_status do_backward(srn_handle* h, void* stream, const float* xyz, const floa
     e = srn::launch_density(L, md, br, tws, xyz, h->cfg.density_eps);
     if (e != cudaSuccess) return cuda_fail(e, "density kernels");
   }
-  e = srn::launch_finalize(L, br, md, tws, dens, h->t.grads_dev + h->lay.off_G,
-                           h->lay.size_G, losses);
-  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel");
-  return SRN_OK;
+  return do_finalize(h, stream, br, flags, losses);
 }
 
-srn_status do_step(srn_handle* h, void* stream, uint32_t flags) {
+srn_status do_step(srn_handle* h, void* stream, uint32_t flags, int seg0 = 0, int seg1 = 5, bool advance = true) {
   const srn_config& c = h->cfg;
   const srn_layout& ly = h->lay;
   srn::AdamLayout al{};
@@ -347,7 +361,7 @@ srn_status do_step(srn_handle* h, void* stream, uint32_t flags) {
                                    h->t.adam_v_dev, c.precision == SRN_BF16 ? h->t.shadow_dev : nullptr,
                                    (flags & SRN_DENSITY) != 0, c.lr_feat, c.lr_xform, c.beta1, c.beta2,
                                    c.adam_eps, h->state(), sch ? h->sched() : nullptr,
-                                   sch ? h->sched_cfg.plateau_factor : 1.f);
+                                   sch ? h->sched_cfg.plateau_factor : 1.f, seg0, seg1, advance);
   if (e != cudaSuccess) return cuda_fail(e, "adam kernel");
   return SRN_OK;
 }
@@ -381,9 +395,20 @@ srn_status enqueue_train_step(srn_handle* h, void* stream, uint64_t seed, const 
   if (e != cudaSuccess) return cuda_fail(e, "sampler");
   e = srn::launch_target(L, br, vol, dims[0], dims[1], dims[2], vb, xyz, target);
   if (e != cudaSuccess) return cuda_fail(e, "target lookup");
-  srn_status st = do_backward(h, stream, xyz, target, br, flags, losses);
+  // BF16 with the density loss: Adam of F and the decoder runs while the density
+  // gradient (second stream) finishes; the transforms' Adam after the finalisation
+  const bool split = h->cfg.precision == SRN_BF16 && h->side.stream && (flags & (SRN_DENSITY | SRN_SCHEDULE));
+  srn_status st = do_backward(h, stream, xyz, target, br, flags, losses, split);
   if (st != SRN_OK) return st;
-  if ((st = do_step(h, stream, flags)) != SRN_OK) return st;
+  if (split) {
+    if ((st = do_step(h, stream, flags, 0, 4, true)) != SRN_OK) return st;
+    e = cudaStreamWaitEvent(L.stream, h->side.join, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "join");
+    if ((st = do_finalize(h, stream, br, flags, losses)) != SRN_OK) return st;
+    if ((st = do_step(h, stream, flags, 4, 5, false)) != SRN_OK) return st;
+  } else if ((st = do_step(h, stream, flags)) != SRN_OK) {
+    return st;
+  }
   if (flags & SRN_SCHEDULE) {
     e = srn::launch_schedule(L, h->cfg.n_bricks, h->sched(), h->sring(), losses, h->sched_params(), h->cfg.beta1,
                              h->cfg.beta2);
