@@ -43,8 +43,8 @@ KERNELS_PER_STEP = {"bf16": 14, "fp32": 10}
 # capture summarised in profiles/train_kernels_dd8.txt (the same 8-brick batch and
 # model).  They hold only for the kernel sources they were taken on: any change to those
 # files makes bench report traffic as null until a new capture.
-NCU_TRAFFIC = {"sources_sha1": "4a6a0fd1cd993c83a41b32eef3170de21bf8baae",
-               "k_scat": 1041.7e6, "k_enc": 726.7e6, "k_mlp": 1333.5e6}
+NCU_TRAFFIC = {"sources_sha1": "bd15e1ed59583666ae5bb0060e6acb65d7630615",
+               "k_scat": 1046.4e6, "k_enc": 716.6e6, "k_mlp": 1333.4e6}
 TRAFFIC_SOURCES = ("k_train_bf16.cu", "k_mlp_tc.cu", "common.cuh", "bf16_ops.cuh", "tc_ops.cuh")
 
 
@@ -65,8 +65,8 @@ def kernel_rooflines(wl, n_total, kt, hbm, tf_sus, src):
     algo = {
         "k_scat": ("hbm", n_total * (12 + m * c * 2) + 2 * 4 * grid_vals,
                    "xyz (12 B) + dL/dy (M*C bf16) per point; read+write of every FP32 feature-gradient grid"),
-        "k_enc": ("hbm", n_total * (12 + k * 2 + 4) + 2 * grid_vals,
-                  "xyz (12 B) + features y (K bf16) + rho (4 B) per point; every BF16 feature grid once"),
+        "k_enc": ("hbm", n_total * (12 + k * 2) + 2 * grid_vals,
+                  "xyz (12 B) + features y (K bf16) per point; every BF16 feature grid once"),
         "k_mlp": ("tensor", n_total * FLOP_PER_POINT, f"{FLOP_PER_POINT} flop per point (decoder fwd+bwd MACs x2)"),
     }
     out = {}
