@@ -68,6 +68,7 @@ struct TrainWs {
   __nv_bfloat16* Y;   // [N][K] features (BF16 training pass)
   __nv_bfloat16* dY;  // [N][M][C] dL/dy, point-major like Y (BF16 training pass)
   int32_t* ustart;    // [B][kUnits + 1] first point of each Morton unit (BF16 scatter tiles)
+  const uint32_t* bin_start;   // [B][kSortBins] the sampler's bin starts of this batch, or NULL
   struct ScatTile* tiles;  // scatter tiles (BF16 training pass)
   int32_t* tile_ctr;  // [0] tiles written, [1] next tile to take
   const struct BrickSched* sched;   // per-brick training routine, or NULL (caller's flags)

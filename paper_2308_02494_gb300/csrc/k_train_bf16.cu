@@ -497,7 +497,9 @@ __global__ void __launch_bounds__(1024) k_tile_list(Bricks brp, TrainWs ws, Mode
     int32_t m = INT_MAX;
 #pragma unroll
     for (int k = UPT - 1; k >= 0; --k) {
-      const int32_t v = us[tid * UPT + k];
+      // a batch from the sampler: unit u starts where its first bin starts
+      const int32_t v = ws.bin_start ? (int32_t)ws.bin_start[(int64_t)b * kSortBins + ((tid * UPT + k) << 3)]
+                                     : us[tid * UPT + k];
       if (v >= 0) m = min(m, v);
       loc[k] = m;
     }
@@ -1205,12 +1207,14 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     int64_t nmax = 0;
     for (int b = 0; b < br.n; ++b) nmax = std::max<int64_t>(nmax, br.off[b + 1] - br.off[b]);
     if (nmax > INT32_MAX) return cudaErrorInvalidValue;
-    if ((e = cudaMemsetAsync(ws.ustart, 0xff, sizeof(int32_t) * (kUnits + 1) * br.n, L.stream)) != cudaSuccess)
-      return e;
     if ((e = cudaMemsetAsync(ws.tile_ctr, 0, 3 * sizeof(int32_t), L.stream)) != cudaSuccess) return e;
-    const int bx = (int)std::min<int64_t>((nmax + 255) / 256, 4 * L.num_sms / std::max(1, br.n) + 1);
-    k_unit_starts<<<dim3(bx, br.n), 256, 0, L.stream>>>(br, xyz, ws.ustart);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!ws.bin_start) {   // else the sampler's histogram gives the unit starts
+      if ((e = cudaMemsetAsync(ws.ustart, 0xff, sizeof(int32_t) * (kUnits + 1) * br.n, L.stream)) != cudaSuccess)
+        return e;
+      const int bx = (int)std::min<int64_t>((nmax + 255) / 256, 4 * L.num_sms / std::max(1, br.n) + 1);
+      k_unit_starts<<<dim3(bx, br.n), 256, 0, L.stream>>>(br, xyz, ws.ustart);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const int cap = std::min(scat_capn(md.M, md.C), enc_capn(md.M, md.C));   // both kernels' boxes fit
     if (cap < 8) return cudaErrorInvalidConfiguration;
     k_tile_list<<<br.n, 1024, 0, L.stream>>>(br, ws, md, cap, kTileLevelCap);

@@ -102,7 +102,8 @@ cudaError_t launch_adam(const Launch& L, const AdamLayout& lay, float* p, float*
                         bool advance = true);
 cudaError_t launch_shadow(const Launch& L, const float* p, uint16_t* shadow, int64_t n);
 
-// Sampler (Philox + Morton counting sort) and ground-truth lookup.
+// Sampler (Philox + Morton counting sort) and ground-truth lookup.  The scanned
+// histogram the sampler leaves in `hist` holds each brick's bin starts.
 cudaError_t launch_sample(const Launch& L, const Bricks& br, unsigned long long seed,
                           unsigned long long step, const unsigned long long* step_dev,
                           float* xyz, float* tmp, uint32_t* rank, uint32_t* hist);

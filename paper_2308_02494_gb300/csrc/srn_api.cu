@@ -168,6 +168,9 @@ struct srn_handle {
   int64_t timed_launches = 0;
   // BF16 training: a second stream for the density passes beside the scatter
   srn::SideStream side{nullptr, nullptr, nullptr, nullptr, false};
+  // set by the training step around its backward pass: the batch is the sampler's, whose
+  // histogram holds the bin starts the BF16 tile list needs
+  const uint32_t* batch_bins = nullptr;
 
   srn::StepState* state() const { return reinterpret_cast<srn::StepState*>(ws + wl.state); }
   srn::BrickSched* sched() const { return reinterpret_cast<srn::BrickSched*>(ws + wl.sched); }
@@ -195,6 +198,7 @@ struct srn_handle {
     w.tile_ctr = reinterpret_cast<int32_t*>(ws + wl.tile_ctr);
     w.sched = nullptr;
     w.eps = cfg.density_eps;
+    w.bin_start = batch_bins;
     return w;
   }
   srn::Model model() const {
@@ -388,17 +392,20 @@ srn_status enqueue_train_step(srn_handle* h, void* stream, uint64_t seed, const 
                               uint32_t flags, float* xyz, float* target, double* losses) {
   const srn::Launch L = h->launch(stream);
   unsigned char* ws = h->ws;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(ws + h->wl.sort_hist);
   cudaError_t e = srn::launch_sample(L, br, seed, 0, &h->state()->step, xyz,
                                      reinterpret_cast<float*>(ws + h->wl.sort_tmp),
-                                     reinterpret_cast<uint32_t*>(ws + h->wl.sort_rank),
-                                     reinterpret_cast<uint32_t*>(ws + h->wl.sort_hist));
+                                     reinterpret_cast<uint32_t*>(ws + h->wl.sort_rank), hist);
   if (e != cudaSuccess) return cuda_fail(e, "sampler");
+  // v(x) on the sorted batch (the volume reads of neighbouring points then share lines)
   e = srn::launch_target(L, br, vol, dims[0], dims[1], dims[2], vb, xyz, target);
   if (e != cudaSuccess) return cuda_fail(e, "target lookup");
   // BF16 with the density loss: Adam of F and the decoder runs while the density
   // gradient (second stream) finishes; the transforms' Adam after the finalisation
   const bool split = h->cfg.precision == SRN_BF16 && h->side.stream && (flags & (SRN_DENSITY | SRN_SCHEDULE));
+  h->batch_bins = hist;
   srn_status st = do_backward(h, stream, xyz, target, br, flags, losses, split);
+  h->batch_bins = nullptr;
   if (st != SRN_OK) return st;
   if (split) {
     if ((st = do_step(h, stream, flags, 0, 4, true)) != SRN_OK) return st;
