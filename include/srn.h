@@ -177,7 +177,12 @@ srn_status srn_sample_target(srn_handle* h, void* stream, const float* volume_de
 srn_status srn_forward(srn_handle* h, void* stream, const float* xyz_dev,
                        const int64_t* offsets, float* out_dev);
 
-/* Forward, L_rec (Sec. 4.3.1) and its gradient into F and the decoder (step (1) of
+/* BF16 handles run the density passes of srn_backward / srn_train_step on a second
+ * stream of their own, created by srn_create: it is forked from and joined back into
+ * the caller's stream within the call, so work that the caller orders after the call
+ * on `stream` sees every result.
+ *
+ * Forward, L_rec (Sec. 4.3.1) and its gradient into F and the decoder (step (1) of
  * Sec. 4.3.2), written (not accumulated) into the gradient buffer.  With
  * SRN_UPSTREAM the gradient is instead that of any loss whose dL/df is given.  With
  * SRN_DENSITY it also evaluates L_den (Eq. 7-9, with h(x) = (f(x) - v(x))^2 and the
@@ -197,7 +202,10 @@ srn_status srn_step(srn_handle* h, void* stream, uint32_t flags);
 /* One whole training iteration: sample -> target -> backward -> Adam, with the
  * sampler step read from the device counter that srn_step advances.  On a
  * non-default stream the sequence is captured once per (flags, offsets, volume)
- * into a CUDA graph and replayed.  losses_dev as in srn_backward. */
+ * into a CUDA graph and replayed.  losses_dev as in srn_backward.  On the BF16 path
+ * with the density loss the Adam step of F and the decoder runs while the gradient
+ * of L_den into G is still being formed (G's Adam step follows it); the results are
+ * those of the sequence above. */
 srn_status srn_train_step(srn_handle* h, void* stream, uint64_t seed, const float* volume_dev,
                           const int64_t dims[3], const int64_t* boxes, const int64_t* offsets,
                           uint32_t flags, float* xyz_dev, float* target_dev, double* losses_dev);
