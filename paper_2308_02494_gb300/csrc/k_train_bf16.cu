@@ -794,23 +794,17 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
 }
 
 // =============================================================================== k_enc
-// Encoder (Eq. 1-3) and the feature density of Eq. 7 on the scatter's tiles.  Lane l of a
-// warp takes grid l of a group of 32 (ScatMap).  Each grid's node box of the tile's block
-// is staged in shared memory as BF16 node values (C per entry), node by node with one
-// column per lane, so the eight corner reads of a warp fall in 32 different banks and the
-// warp's features of one point form one coalesced store of Y.  Points outside their box
-// (rounding at its faces; an unsorted batch) and grids whose box does not fit read the
-// corners from global memory.  The density rho of a point sums det(A_i) E_i over the
-// grids: with M >= 32 the warp adds its 32 lanes' terms as fixed-point integers (one
-// reduction instruction; a power-of-two scale per brick keeps every term below 2^21),
-// with M < 32 by shuffles, and the groups' integer partial sums meet in the point's staged
-// slot (a shared-memory integer reduction).
+// Encoder (Eq. 1-3) on the scatter's tiles.  Lane l of a warp takes grid l of a group of
+// 32 (ScatMap).  Each grid's node box of the tile's block is staged in shared memory as
+// BF16 node values (C per entry), node by node with one column per lane, so the eight
+// corner reads of a warp fall in 32 different banks and the warp's features of one point
+// form one coalesced store of Y.  Points outside their box (rounding at its faces; an
+// unsorted batch) and grids whose box does not fit read the corners from global memory.
+// The feature density of Eq. 7 is a pass of its own (k_density_rho).
 struct EncHead {
-  float4 xs[ST];                // the tile's points; .w collects rho
+  float4 xs[ST];                // the tile's points
   uint2 box[kMaxGrids];         // node box of the tile's block per grid (as in the scatter)
   float gs[kMaxGrids * 12];     // the brick's transforms
-  float det[kMaxGrids];         // their determinants
-  float dscale, dinv;           // fixed-point scale of the density terms and its inverse
   ScatTile tile;
 };
 template <int C>
@@ -848,8 +842,7 @@ __device__ __noinline__ uint32_t enc_global(const __nv_bfloat16* Fi, Cell c, int
   return C == 2 ? pack_bf16(f0, f1) : (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f0));
 }
 
-// P10: the paper's flat-top exponent p = 10 at compile time (DENS only).
-template <int C, bool DENS, bool P10>
+template <int C>
 __global__ void __launch_bounds__(SNT, 2)
 k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn) {
   using E = EncNode<C>;
@@ -869,13 +862,7 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn)
   // staging: M >= 32, the warps of a group split the nodes of their grids; M < 32, every
   // lane fills its own column and all warps split the nodes
   const int n0 = M >= 32 ? mp.pg : warp, nstep = M >= 32 ? mp.npg : SNW;
-  double sum_rho = 0.0;
   int cur = -1;
-  auto flush = [&](int b) {
-    double s = warp_sum(sum_rho);
-    if (lane == 0) atomicAdd(ws.acc + b * kAccPerBrick + ACC_SUM_RHO, s);
-    sum_rho = 0.0;
-  };
   for (;;) {
     if (tid == 0) {
       const int t = atomicAdd(ws.tile_ctr + 2, 1);
@@ -890,29 +877,8 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn)
     const int b = (int)(T.code >> 20);
     const float* Gb = md.G + (int64_t)b * md.sG;
     if (b != cur) {
-      if (DENS && cur >= 0) flush(cur);
       cur = b;
       for (int c = tid; c < M * 12; c += SNT) h.gs[c] = Gb[c];
-      if (DENS && warp == 0) {
-        float m = 0.f;
-        for (int i = lane; i < M; i += 32) {
-          const float d = det3(Gb + 12 * i);
-          h.det[i] = d;
-          m = fmaxf(m, fabsf(d));
-        }
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 8));
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-        if (lane == 0) {   // |det E| 2^S < 2^21 for every grid (E <= 1)
-          int ex = 0;
-          frexpf(m, &ex);   // m < 2^ex
-          const int S = max(-100, min(100, 21 - ex));
-          h.dscale = ldexpf(1.f, S);
-          h.dinv = ldexpf(1.f, -S);
-        }
-      }
     }
     const int64_t p0 = T.start;
     const int np = T.count;
@@ -954,50 +920,16 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn)
     float gi[12];
 #pragma unroll
     for (int j = 0; j < 12; ++j) gi[j] = h.gs[12 * mp.g + j];
-    const float dq = DENS ? h.det[mp.g] * h.dscale : 0.f;   // det E 2^S + kMagic: round(det E 2^S) in the low bits
-    const float dinv = DENS ? h.dinv : 0.f;   // (the slots start at integer 0: xs[p].w = 0.f)
     __syncthreads();
     const uint32_t col_s = su32(col);
     const uint32_t oy = (uint32_t)nxb * kRow, oz = (uint32_t)(nxb * nyb) * kRow;   // bytes
     E* Yt = reinterpret_cast<E*>(ws.Y) + p0 * M + mp.g;
     const __nv_bfloat16* Fi = md.F16 + (int64_t)b * md.sF + mp.g * gsz;
-    // the warp steps through its points together (M < 32: its 32/M lane groups take
-    // consecutive points), so the density reductions always see the whole warp
-    const int sub = M >= 32 ? 0 : lane / M;
 #pragma unroll 2
-    for (int pb = mp.pg - sub; pb < np; pb += mp.npg) {
-      const int p = pb + sub;
-      const bool valid = p < np;
-      const float4 x = h.xs[valid ? p : 0];
+    for (int p = mp.pg; p < np; p += mp.npg) {
+      const float4 x = h.xs[p];
       float ux, uy, uz;
       affine(gi, x.x, x.y, x.z, ux, uy, uz);
-      if constexpr (DENS) {   // det E 2^S as an integer; the warp's (group's) sum into the point's slot
-        float t;
-        if constexpr (P10) {   // exp(-sum_d u_d^20), the x and y axes as a packed pair
-          const f2_t uxy = f2_pack(ux, uy), s2 = f2_mul(uxy, uxy);
-          f2_t q = f2_mul(s2, s2);
-          q = f2_mul(q, q);
-          q = f2_mul(q, q);
-          const f2_t p20 = f2_mul(f2_mul(q, s2), s2);
-          const float z2 = uz * uz;
-          float pz = z2 * z2;
-          pz = pz * pz;
-          pz = pz * pz;
-          const float ssum = fmaf(pz * z2, z2, f2_lo(p20) + f2_hi(p20));
-          t = valid && ssum <= 87.f ? __expf(-ssum) : 0.f;
-        } else {
-          t = valid ? flat_top(ux, uy, uz, md.p) : 0.f;
-        }
-        int32_t v = __float_as_int(fmaf(t, dq, kMagic)) - kMagicBits;
-        if (M >= 32) {
-          v = __reduce_add_sync(0xffffffffu, v);
-          if (lane == 0) red_s32<0>(su32(&h.xs[p].w), v);
-        } else {
-          for (int o = M >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (valid && lane % M == 0) red_s32<0>(su32(&h.xs[p].w), v);
-        }
-      }
-      if (!valid) continue;
       uint32_t yv = 0u;
       if ((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f)) {
         // Eq. 2's set-up as make_cell computes it: inside the grid s lies in [0, R-1] (the
@@ -1037,16 +969,7 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn)
       }
       Yt[p * M] = (E)yv;
     }
-    if constexpr (DENS) {
-      __syncthreads();
-      for (int p = tid; p < np; p += SNT) {
-        const float rho = (float)__float_as_int(h.xs[p].w) * dinv;   // the slot holds sum det E 2^S
-        ws.rho[p0 + p] = rho;
-        sum_rho += (double)rho;
-      }
-    }
   }
-  if (DENS && cur >= 0) flush(cur);
 }
 
 // =============================================================================== k_rec_dg
@@ -1187,7 +1110,7 @@ int enc_capn(int M, int C) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, (const void*)k_enc<2, true, true>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
+  if (cudaFuncGetAttributes(&fa, (const void*)k_enc<2>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
   const int ngrp = M >= 32 ? M / 32 : 1;
   const long long room = (long long)per_sm / 2 - 1024 - stat - (long long)sizeof(EncHead);
   return room > 0 ? (int)(room / ((long long)ngrp * 32 * (C == 2 ? 4 : 2))) : 0;
@@ -1223,12 +1146,7 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
   {
     const int capn = enc_capn(md.M, md.C);
     const size_t smem = enc_smem(md.M, md.C, capn);
-    const bool p10 = md.p == 10;
-    const bool edens = dens && !side;   // with the second stream, rho is its first pass
-    const void* kern = md.C == 2 ? (edens ? (p10 ? (const void*)k_enc<2, true, true> : (const void*)k_enc<2, true, false>)
-                                          : (const void*)k_enc<2, false, true>)
-                                 : (edens ? (p10 ? (const void*)k_enc<1, true, true> : (const void*)k_enc<1, true, false>)
-                                          : (const void*)k_enc<1, false, true>);
+    const void* kern = md.C == 2 ? (const void*)k_enc<2> : (const void*)k_enc<1>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
     const int grid = L.num_sms * occupancy(kern, SNT, smem);
@@ -1239,6 +1157,8 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
       if ((e = cudaEventRecord(side->enc_done, L.stream)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(side->stream, side->enc_done, 0)) != cudaSuccess) return e;
       if ((e = launch_density_rho(Launch{side->stream, L.num_sms}, md, br, ws, xyz)) != cudaSuccess) return e;
+    } else if (dens && (e = launch_density_rho(L, md, br, ws, xyz)) != cudaSuccess) {
+      return e;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark_stop(0);
