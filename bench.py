@@ -34,9 +34,10 @@ MLP_MACS_FWD = 128 * 64 + 64 * 64 + 64
 MLP_MACS_BWD = 64 * 64 + 64 * 64 + 64 * 128 + 64 * 128 + 64
 FLOP_PER_POINT = 2 * (MLP_MACS_FWD + MLP_MACS_BWD)
 # kernels of one training step: sampler (3), target lookup, the query pass (BF16: scatter
-# tile list (2), encoder, decoder, scatter; FP32: 1 fused kernel), density passes (2),
-# finalisation, step counter, Adam
-KERNELS_PER_STEP = {"bf16": 14, "fp32": 10}
+# tile list (the unit starts come from the sampler), encoder, decoder, scatter; FP32: 1
+# fused kernel), density passes (BF16: 3 on the second stream; FP32: 2), finalisation,
+# step counter, Adam (BF16 density steps: F and the decoder, then G)
+KERNELS_PER_STEP = {"bf16": 15, "fp32": 10}
 
 
 # DRAM bytes (read + write) per launch of each training-pass kernel, from the ncu
