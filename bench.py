@@ -44,7 +44,7 @@ KERNELS_PER_STEP = {"bf16": 15, "fp32": 10}
 # capture summarised in profiles/train_kernels_dd8.txt (the same 8-brick batch and
 # model).  They hold only for the kernel sources they were taken on: any change to those
 # files makes bench report traffic as null until a new capture.
-NCU_TRAFFIC = {"sources_sha1": "4ba93c0dd5e5f5ce562f87d6832f6a98c145dcfc",
+NCU_TRAFFIC = {"sources_sha1": "88f06b4dc3481774285c3f7807f6cd8007321e38",
                "k_scat": 1037.7e6, "k_enc": 716.1e6, "k_mlp": 1333.7e6}
 TRAFFIC_SOURCES = ("k_train_bf16.cu", "k_mlp_tc.cu", "common.cuh", "bf16_ops.cuh", "tc_ops.cuh")
 
@@ -94,6 +94,9 @@ def parse():
     ap.add_argument("--workload", choices=["dd8", "single-bf16", "single-fp32"], default="dd8")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32-plain and e2e legs")
+    ap.add_argument("--tiles", choices=["auto", "default"], default="auto",
+                    help="BF16 tile shape: picked by srn_autotune on one batch before warm-up, or the "
+                         "library default")
     ap.add_argument("--volume", type=int, default=None,
                     help="voxels per axis of the synthetic volume (default: the workload's); a smaller "
                          "volume keeps the same batch and model with a small device footprint, for profilers")
@@ -367,6 +370,14 @@ def run_own(args, workload):
     # every rank trains its own bricks: different models and uneven batch sizes per rank
     m, vol, boxes, off, xyz, tgt, n_total = setup(wl, seed_offset=rank)
     stream = torch.cuda.Stream()
+    tiles = None
+    if wl["precision"] == "bf16":
+        if args.tiles == "auto":   # the library's tuner on one batch of the workload, before any timing
+            m.sample_points(5, 0, off, xyz)
+            m.sample_target(vol, boxes, xyz, off, tgt)
+            tiles = dict(m.autotune(xyz, tgt, off, density=True, reps=3), picked_by="srn_autotune")
+        else:
+            tiles = dict(m.tuning, picked_by="library default")
     clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     # warm up (first call eager, second captures the CUDA graph, the rest replay it)
     time_steps(m, vol, boxes, off, xyz, tgt, 0, max(3, args.warmup), stream, sync_all)
@@ -463,6 +474,8 @@ def run_own(args, workload):
     cfg = dict(wl)
     cfg["points_per_step"] = points_all // args.steps
     cfg["parallelism"] = f"{world} GPUs, each training its own 8 bricks (no collective)" if world > 1 else "1 GPU"
+    if tiles:
+        cfg["tiles"] = tiles
     if render:
         cfg["render"] = render
     if decode:

@@ -317,6 +317,44 @@ srn_status srn_decode(srn_handle* h, void* stream, const int32_t grid[3], const 
 srn_status srn_set_timing(srn_handle* h, int32_t target);
 srn_status srn_read_timing(srn_handle* h, double* total_ms, int64_t* launches);
 
+/* Launch shape of the BF16 training pass (no counterpart in the paper; the paper's
+ * encoder and scatter are library kernels).  The pass cuts each brick's Morton-sorted
+ * points into tiles: runs of consecutive points inside one aligned Morton block of at
+ * most 2^tile_level units (a unit is 1/16 of the domain per axis), holding at most
+ * tile_points points, and within that block's node box in every grid (a brick's level is
+ * further capped so that its boxes fit the kernels' shared memory).  density_ctas is the
+ * CTAs per SM of the density-gradient pass that runs beside the scatter.  Every tuning
+ * gives the same results up to the rounding of the fixed-point gradient sums (their
+ * quantum is set per tile and grid).  The default, set by srn_create, is
+ * {1024, 9, 2}.
+ *   srn_get_tuning  copies the handle's tuning to *out.
+ *   srn_set_tuning  installs *t: 128 <= tile_points <= 1024 and a multiple of 32,
+ *                   0 <= tile_level <= 9, 1 <= density_ctas <= 4, else
+ *                   SRN_ERR_INVALID_ARG.  Training steps captured in CUDA graphs by
+ *                   srn_train_step are re-captured.  FP32 handles store it unused.
+ *   srn_autotune    picks the tile shape (tile_points, tile_level) of a BF16 handle by
+ *                   timing srn_backward(stream, xyz_dev, target_dev, offsets, flags) for
+ *                   each candidate of a fixed set ({256, 512, 768, 1024} points x
+ *                   levels {2, 3, 4, 6, 9}), the handle's current tuning first: each
+ *                   candidate runs once untimed, then `reps` (1..100) times bracketed by
+ *                   CUDA events on `stream`; its score is the median, and a candidate
+ *                   replaces the best so far only when at least 1% faster.  It installs
+ *                   the winner as srn_set_tuning does, writes it to *out (may be NULL),
+ *                   then runs srn_backward once more with it, so that the gradient buffer
+ *                   holds that pass's gradient.  Parameters, Adam moments and step
+ *                   counters are not touched.  Synchronises `stream`; not allowed while
+ *                   `stream` is being captured (SRN_ERR_STATE) or on FP32 handles
+ *                   (SRN_ERR_UNSUPPORTED).  Arguments otherwise as srn_backward. */
+typedef struct {
+  int32_t tile_points;
+  int32_t tile_level;
+  int32_t density_ctas;
+} srn_tuning;
+srn_status srn_get_tuning(srn_handle* h, srn_tuning* out);
+srn_status srn_set_tuning(srn_handle* h, const srn_tuning* t);
+srn_status srn_autotune(srn_handle* h, void* stream, const float* xyz_dev, const float* target_dev,
+                        const int64_t* offsets, uint32_t flags, int32_t reps, srn_tuning* out);
+
 /* Synchronise `stream` and report device-side status since the last call (then clear
  * it): SRN_ERR_DEVICE_TIMEOUT if a kernel gave up a bounded wait on the tensor cores
  * (its outputs are then invalid), else SRN_ERR_NONFINITE if a loss was NaN/Inf, else

@@ -357,10 +357,9 @@ k_mlp(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ targ
 }
 
 // =============================================================================== k_scat
-constexpr int ST = 1024;        // Morton-consecutive points per scatter tile (at most)
+constexpr int ST = kMaxTilePoints;   // Morton-consecutive points per tile (at most)
 constexpr int SNT = 512;        // threads of k_scat (one CTA per SM)
 constexpr int SNW = SNT / 32;
-constexpr int kTileLevelCap = 9;            // largest Morton level of a scatter tile
 constexpr float kMagic = 12582912.f;        // 1.5 * 2^23: for |x| < 2^22, x + kMagic holds round(x)
 constexpr int32_t kMagicBits = 0x4B400000;  // in its low bits, offset by these bits of kMagic
 
@@ -460,9 +459,10 @@ __global__ void k_unit_starts(Bricks brp, const float* __restrict__ xyz, int32_t
 // take the next recorded one (a suffix minimum; for a sorted batch this is exact, for any
 // batch the starts become non-decreasing from 0 to n, so the tiles below always partition
 // the brick's points).  Every unit then belongs to the largest aligned range of 2^L units
-// (L <= lmax) holding at most ST points; each such range becomes ceil(points / ST) tiles
-// of consecutive points.
-__global__ void __launch_bounds__(1024) k_tile_list(Bricks brp, TrainWs ws, Model md, int capn, int lcap) {
+// (L <= lmax) holding at most tp (<= ST) points; each such range becomes ceil(points / tp)
+// tiles of consecutive points.
+__global__ void __launch_bounds__(1024) k_tile_list(Bricks brp, TrainWs ws, Model md, int capn, int lcap,
+                                                    int tp) {
   constexpr int UPT = kUnits / 1024;
   __shared__ Bricks br;
   __shared__ int32_t st[kUnits + 1];
@@ -530,11 +530,11 @@ __global__ void __launch_bounds__(1024) k_tile_list(Bricks brp, TrainWs ws, Mode
     int L = 0;
     for (int l = lmax; l > 0; --l) {
       const int a = u & ~((1 << l) - 1);
-      if (st[a + (1 << l)] - st[a] <= ST) { L = l; break; }
+      if (st[a + (1 << l)] - st[a] <= tp) { L = l; break; }
     }
     lv[k] = L;
     nt[k] = 0;
-    if ((u & ((1 << L) - 1)) == 0) nt[k] = (st[u + (1 << L)] - st[u] + ST - 1) / ST;
+    if ((u & ((1 << L) - 1)) == 0) nt[k] = (st[u + (1 << L)] - st[u] + tp - 1) / tp;
     tot += nt[k];
   }
   int incl = tot;   // block-wide exclusive scan of the tile counts
@@ -1118,8 +1118,8 @@ int enc_capn(int M, int C) {
 
 template <int K>
 cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
-                           const TrainWs& ws, const float* xyz, const float* target, const KernelMark* mark,
-                           const SideStream* side) {
+                           const TrainWs& ws, const float* xyz, const float* target, const Tuning& tn,
+                           const KernelMark* mark, const SideStream* side) {
   auto mark_start = [&](int k) { if (mark && mark->which == k) cudaEventRecord(mark->start, L.stream); };
   auto mark_stop = [&](int k) { if (mark && mark->which == k) cudaEventRecord(mark->stop, L.stream); };
   int tiles = 0;
@@ -1140,7 +1140,9 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     }
     const int cap = std::min(scat_capn(md.M, md.C), enc_capn(md.M, md.C));   // both kernels' boxes fit
     if (cap < 8) return cudaErrorInvalidConfiguration;
-    k_tile_list<<<br.n, 1024, 0, L.stream>>>(br, ws, md, cap, kTileLevelCap);
+    if (tn.tile_points < kMinTilePoints || tn.tile_points > ST || tn.tile_level < 0 || tn.tile_level > kMaxTileLevel)
+      return cudaErrorInvalidValue;
+    k_tile_list<<<br.n, 1024, 0, L.stream>>>(br, ws, md, cap, tn.tile_level, tn.tile_points);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -1178,12 +1180,12 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     mark_stop(1);
   }
   if (dens && side) {   // the other two density passes beside the scatter, after the decoder
-    // two CTAs per SM taking tiles from a counter: one fits beside the scatter's CTA
-    // (registers and the shared memory scat_capn leaves), the other starts as the
-    // scatter's CTA finishes and leaves room for the Adam of F and the decoder, which the
-    // training step runs beside this pass's tail (measured: 3.43 ms per step against
-    // 3.48 with four CTAs per SM, whose registers fill the SM)
-    const int ctas = 2;
+    // CTAs taking tiles from a counter, tn.density_ctas per SM (default two): one fits
+    // beside the scatter's CTA (registers and the shared memory scat_capn leaves), the
+    // other starts as the scatter's CTA finishes and leaves room for the Adam of F and
+    // the decoder, which the training step runs beside this pass's tail (measured: 3.43 ms
+    // per step against 3.48 with four CTAs per SM, whose registers fill the SM)
+    const int ctas = std::min(std::max(tn.density_ctas, 1), kMaxDensityCtas);
     if ((e = cudaEventRecord(side->fork, L.stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(side->stream, side->fork, 0)) != cudaSuccess) return e;
     if ((e = launch_density(Launch{side->stream, L.num_sms}, md, br, ws, xyz, ws.eps, ctas)) != cudaSuccess) return e;
@@ -1217,13 +1219,13 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
 }  // namespace
 
 cudaError_t launch_train_bf16(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
-                              const TrainWs& ws, const float* xyz, const float* target, const KernelMark* mark,
-                              const SideStream* side) {
+                              const TrainWs& ws, const float* xyz, const float* target, const Tuning& tn,
+                              const KernelMark* mark, const SideStream* side) {
   switch (md.K) {
-    case 16: return launch_train_k<16>(L, dens, md, gr, br, ws, xyz, target, mark, side);
-    case 32: return launch_train_k<32>(L, dens, md, gr, br, ws, xyz, target, mark, side);
-    case 64: return launch_train_k<64>(L, dens, md, gr, br, ws, xyz, target, mark, side);
-    case 128: return launch_train_k<128>(L, dens, md, gr, br, ws, xyz, target, mark, side);
+    case 16: return launch_train_k<16>(L, dens, md, gr, br, ws, xyz, target, tn, mark, side);
+    case 32: return launch_train_k<32>(L, dens, md, gr, br, ws, xyz, target, tn, mark, side);
+    case 64: return launch_train_k<64>(L, dens, md, gr, br, ws, xyz, target, tn, mark, side);
+    case 128: return launch_train_k<128>(L, dens, md, gr, br, ws, xyz, target, tn, mark, side);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -32,8 +32,22 @@ struct SideStream {
   cudaEvent_t fork, join, enc_done;
   bool defer_join;   // the caller waits for `join` itself (later work can run beside the tail)
 };
+// Launch shape of the BF16 training pass, set per handle (srn_set_tuning, srn_autotune).
+// A tile is a run of Morton-consecutive points of one brick inside one aligned Morton
+// block of at most 2^tile_level units, holding at most tile_points points; the block's
+// node box in every grid is what the encoder stages and the scatter accumulates.
+constexpr int kMinTilePoints = 128;
+constexpr int kMaxTilePoints = 1024;   // the encoder's and the scatter's point staging
+constexpr int kMaxTileLevel = 9;
+constexpr int kMaxDensityCtas = 4;     // eight warps of 64 registers each fill an SM at 4
+struct Tuning {
+  int tile_points;    // kMinTilePoints .. kMaxTilePoints, a multiple of 32
+  int tile_level;     // 0 .. kMaxTileLevel (each brick further capped by its node boxes)
+  int density_ctas;   // CTAs per SM of the density-gradient pass beside the scatter
+};
+constexpr Tuning kDefaultTuning{kMaxTilePoints, kMaxTileLevel, 2};
 cudaError_t launch_train_bf16(const Launch& L, bool dens, const Model& md, const Grads& gr, const Bricks& br,
-                              const TrainWs& ws, const float* xyz, const float* target,
+                              const TrainWs& ws, const float* xyz, const float* target, const Tuning& tn,
                               const KernelMark* mark = nullptr, const SideStream* side = nullptr);
 // The decoder kernel of the BF16 training pass on the tcgen05 tensor cores (K = 128).
 cudaError_t launch_mlp_tc(const Launch& L, const Model& md, const Grads& gr, const Bricks& br, const TrainWs& ws,

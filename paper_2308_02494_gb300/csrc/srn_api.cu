@@ -102,9 +102,10 @@ WsLayout ws_layout(const srn_config* c, int64_t maxp) {
   const size_t kbytes = c->precision == SRN_BF16 ? sizeof(uint16_t) * c->n_grids * c->channels : 0;
   w.feat = o; o += align256(kbytes * maxp);
   w.dfeat = o; o += align256(kbytes * maxp);
-  // BF16 scatter tiles: unit starts, and at most one tile per unit plus one per 1024 points
+  // BF16 tiles: unit starts, and at most one tile per unit plus one per kMinTilePoints
+  // points (the smallest tile any tuning allows)
   const bool bf16 = c->precision == SRN_BF16;
-  const int64_t max_tiles = (int64_t)c->n_bricks * (srn::kUnits + 1) + maxp / 1024 + 1;
+  const int64_t max_tiles = (int64_t)c->n_bricks * (srn::kUnits + 1) + maxp / srn::kMinTilePoints + 1;
   w.ustart = o; o += bf16 ? align256(sizeof(int32_t) * (srn::kUnits + 1) * c->n_bricks) : 0;
   w.tiles = o; o += bf16 ? align256(sizeof(srn::ScatTile) * max_tiles) : 0;
   w.tile_ctr = o; o += align256(sizeof(int32_t) * 4);
@@ -171,6 +172,8 @@ struct srn_handle {
   // set by the training step around its backward pass: the batch is the sampler's, whose
   // histogram holds the bin starts the BF16 tile list needs
   const uint32_t* batch_bins = nullptr;
+  // launch shape of the BF16 training pass (srn_set_tuning / srn_autotune)
+  srn::Tuning tune = srn::kDefaultTuning;
 
   srn::StepState* state() const { return reinterpret_cast<srn::StepState*>(ws + wl.state); }
   srn::BrickSched* sched() const { return reinterpret_cast<srn::BrickSched*>(ws + wl.sched); }
@@ -298,7 +301,7 @@ srn_status run_query(srn_handle* h, void* stream, srn::QueryMode mode, const srn
   else if (mode == srn::kForward)
     e = srn::launch_forward_bf16(L, md, br, xyz, out);
   else
-    e = srn::launch_train_bf16(L, mode == srn::kTrainDensity, md, gr, br, ws, xyz, target,
+    e = srn::launch_train_bf16(L, mode == srn::kTrainDensity, md, gr, br, ws, xyz, target, h->tune,
                                timed && time_kernel ? &mark : nullptr, h->side.stream ? &h->side : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "query kernel");
   if (timed) {
@@ -975,6 +978,139 @@ srn_status srn_render_progressive(srn_handle* h, void* stream, const srn_camera*
     if (e != cudaSuccess) return cuda_fail(e, "render preview");
   }
   return SRN_OK;
+}
+
+namespace {
+
+srn_status check_tuning(const srn_tuning* t) {
+  if (!t) return fail(SRN_ERR_INVALID_ARG, "tuning is NULL");
+  if (t->tile_points < srn::kMinTilePoints || t->tile_points > srn::kMaxTilePoints || t->tile_points % 32)
+    return fail(SRN_ERR_INVALID_ARG, "tile_points %d is not a multiple of 32 in [%d, %d]", (int)t->tile_points,
+                srn::kMinTilePoints, srn::kMaxTilePoints);
+  if (t->tile_level < 0 || t->tile_level > srn::kMaxTileLevel)
+    return fail(SRN_ERR_INVALID_ARG, "tile_level %d outside [0, %d]", (int)t->tile_level, srn::kMaxTileLevel);
+  if (t->density_ctas < 1 || t->density_ctas > srn::kMaxDensityCtas)
+    return fail(SRN_ERR_INVALID_ARG, "density_ctas %d outside [1, %d]", (int)t->density_ctas,
+                srn::kMaxDensityCtas);
+  return SRN_OK;
+}
+
+// Installs a tuning; the CUDA graphs of srn_train_step hold launches with the old one.
+void install_tuning(srn_handle* h, const srn::Tuning& t) {
+  const srn::Tuning& o = h->tune;
+  if (t.tile_points == o.tile_points && t.tile_level == o.tile_level && t.density_ctas == o.density_ctas) return;
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  h->tune = t;
+}
+
+// Median time in milliseconds of `reps` backward passes under the handle's tuning,
+// after one untimed pass (which also sets the kernels' shared-memory attributes).
+srn_status time_backward(srn_handle* h, void* stream, const float* xyz, const float* target,
+                         const srn::Bricks& br, uint32_t flags, int reps, cudaEvent_t t0, cudaEvent_t t1,
+                         float* median) {
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  srn_status st = do_backward(h, stream, xyz, target, br, flags, nullptr);
+  std::vector<float> ms((size_t)reps, 0.f);
+  for (int r = 0; r < reps && st == SRN_OK; ++r) {
+    cudaError_t e = cudaEventRecord(t0, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune event");
+    if ((st = do_backward(h, stream, xyz, target, br, flags, nullptr)) != SRN_OK) break;
+    e = cudaEventRecord(t1, cs);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[(size_t)r], t0, t1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+  }
+  if (st != SRN_OK) return st;
+  std::sort(ms.begin(), ms.end());
+  const size_t m = (size_t)reps / 2;
+  *median = reps % 2 ? ms[m] : 0.5f * (ms[m - 1] + ms[m]);
+  return SRN_OK;
+}
+
+}  // namespace
+
+srn_status srn_get_tuning(srn_handle* h, srn_tuning* out) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (!out) return fail(SRN_ERR_INVALID_ARG, "NULL output");
+  out->tile_points = h->tune.tile_points;
+  out->tile_level = h->tune.tile_level;
+  out->density_ctas = h->tune.density_ctas;
+  return SRN_OK;
+}
+
+srn_status srn_set_tuning(srn_handle* h, const srn_tuning* t) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if ((s = check_tuning(t)) != SRN_OK) return s;
+  install_tuning(h, srn::Tuning{t->tile_points, t->tile_level, t->density_ctas});
+  return SRN_OK;
+}
+
+srn_status srn_autotune(srn_handle* h, void* stream, const float* xyz, const float* target,
+                        const int64_t* offsets, uint32_t flags, int32_t reps, srn_tuning* out) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  if (h->cfg.precision != SRN_BF16) return fail(SRN_ERR_UNSUPPORTED, "srn_autotune: the FP32 pass has no tiles");
+  if (reps < 1 || reps > 100) return fail(SRN_ERR_INVALID_ARG, "srn_autotune: reps %d outside [1, 100]", (int)reps);
+  srn::Bricks br;
+  if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
+  if ((s = check_training_counts(br)) != SRN_OK) return s;
+  if (!xyz || !target) return fail(SRN_ERR_INVALID_ARG, "xyz or target is NULL");
+  if (flags & ~(SRN_DENSITY | SRN_UPSTREAM | SRN_REC_DG)) return fail(SRN_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  if ((flags & SRN_DENSITY) && (flags & SRN_UPSTREAM))
+    return fail(SRN_ERR_INVALID_ARG, "SRN_DENSITY needs the per-point error, which SRN_UPSTREAM lacks");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(cs, &cap);
+  if (e != cudaSuccess) return cuda_fail(e, "capture status");
+  if (cap != cudaStreamCaptureStatusNone) return fail(SRN_ERR_STATE, "srn_autotune: the stream is being captured");
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e != cudaSuccess) {
+    if (t0) cudaEventDestroy(t0);
+    return cuda_fail(e, "event create");
+  }
+  // candidates: tile sizes, and level caps from small blocks (small boxes, more tiles)
+  // up to the largest (where the shared-memory bound on the boxes decides)
+  static const int kPoints[] = {256, 512, 768, 1024};
+  static const int kLevels[] = {2, 3, 4, 6, 9};
+  const int32_t timing = h->timing;   // the search is not reported by the measurement hook
+  h->timing = SRN_TIME_OFF;
+  const srn::Tuning start = h->tune;
+  srn::Tuning best = start;
+  float best_ms = 0.f;
+  s = time_backward(h, stream, xyz, target, br, flags, reps, t0, t1, &best_ms);
+  for (int tp : kPoints) {
+    for (int lv : kLevels) {
+      if (s != SRN_OK || (tp == start.tile_points && lv == start.tile_level)) continue;
+      h->tune = srn::Tuning{tp, lv, start.density_ctas};
+      float ms = 0.f;
+      if ((s = time_backward(h, stream, xyz, target, br, flags, reps, t0, t1, &ms)) != SRN_OK) break;
+      if (ms < 0.99f * best_ms) {
+        best = h->tune;
+        best_ms = ms;
+      }
+    }
+  }
+  h->tune = start;
+  h->timing = timing;
+  if (s == SRN_OK) {
+    install_tuning(h, best);
+    s = do_backward(h, stream, xyz, target, br, flags, nullptr);
+  }
+  if (s == SRN_OK && (e = cudaStreamSynchronize(cs)) != cudaSuccess) s = cuda_fail(e, "autotune sync");
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (s == SRN_OK && out) {
+    out->tile_points = best.tile_points;
+    out->tile_level = best.tile_level;
+    out->density_ctas = best.density_ctas;
+  }
+  return s;
 }
 
 srn_status srn_get_status(srn_handle* h, void* stream) {

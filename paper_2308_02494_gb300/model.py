@@ -119,6 +119,20 @@ class SRN:
                         flags, self.losses.data_ptr())
         return self.losses
 
+    @property
+    def tuning(self) -> dict:
+        """Launch shape of the BF16 training pass (srn_get_tuning)."""
+        return _s.srn_get_tuning(self.handle)
+
+    def set_tuning(self, tile_points: int, tile_level: int, density_ctas: int) -> None:
+        _s.srn_set_tuning(self.handle, tile_points, tile_level, density_ctas)
+
+    def autotune(self, xyz, target, offsets, density: bool = True, reps: int = 5, stream=None) -> dict:
+        """srn_autotune on one batch: times the backward pass per tile shape, installs the
+        fastest and returns it."""
+        return _s.srn_autotune(self.handle, _stream_ptr(stream), xyz.data_ptr(), target.data_ptr(), offsets,
+                               _s.SRN_DENSITY if density else 0, reps)
+
     def step(self, density: bool = False, stream=None) -> None:
         _s.srn_step(self.handle, _stream_ptr(stream), _s.SRN_DENSITY if density else 0)
 

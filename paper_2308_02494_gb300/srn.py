@@ -35,7 +35,8 @@ EXPORTS = (
     "srn_sync_shadow", "srn_sample_points", "srn_sample_target", "srn_forward", "srn_backward",
     "srn_step", "srn_train_step", "srn_render", "srn_set_timing", "srn_read_timing", "srn_get_status",
     "srn_sample_points_static", "srn_decode", "srn_state_bytes", "srn_save_state", "srn_load_state",
-    "srn_set_schedule", "srn_read_schedule", "srn_render_progressive",
+    "srn_set_schedule", "srn_read_schedule", "srn_render_progressive", "srn_get_tuning", "srn_set_tuning",
+    "srn_autotune",
 )
 SRN_STATIC_SAMPLER_MAX_POINTS = 131072
 SRN_STATIC_SAMPLER_MAX_BRICKS = 8
@@ -65,6 +66,10 @@ class BrickSchedule(ct.Structure):
     _fields_ = [("iteration", ct.c_int64), ("lr_scale", ct.c_float), ("plateaus", ct.c_int32),
                 ("finished", ct.c_int32), ("density_on", ct.c_int32), ("density_stopped", ct.c_int32),
                 ("density_iters", ct.c_int32), ("best_rec", ct.c_double)]
+
+
+class Tuning(ct.Structure):
+    _fields_ = [("tile_points", ct.c_int32), ("tile_level", ct.c_int32), ("density_ctas", ct.c_int32)]
 
 
 class Layout(ct.Structure):
@@ -121,6 +126,9 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
         "srn_read_schedule": [P, P, ct.POINTER(BrickSchedule)],
         "srn_save_state": [P, P, P, ct.c_size_t],
         "srn_load_state": [P, P, P, ct.c_size_t],
+        "srn_get_tuning": [P, ct.POINTER(Tuning)],
+        "srn_set_tuning": [P, ct.POINTER(Tuning)],
+        "srn_autotune": [P, P, P, P, I64P, U32, I32, ct.POINTER(Tuning)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -261,6 +269,22 @@ def srn_save_state(h, stream) -> bytes:
 def srn_load_state(h, stream, blob: bytes) -> None:
     buf = (ct.c_ubyte * len(blob)).from_buffer_copy(blob)
     _check(load().srn_load_state(h, stream, buf, len(blob)))
+
+
+def srn_get_tuning(h) -> dict:
+    out = Tuning()
+    _check(load().srn_get_tuning(h, ct.byref(out)))
+    return {f: getattr(out, f) for f, _ in Tuning._fields_}
+
+
+def srn_set_tuning(h, tile_points, tile_level, density_ctas) -> None:
+    _check(load().srn_set_tuning(h, ct.byref(Tuning(tile_points, tile_level, density_ctas))))
+
+
+def srn_autotune(h, stream, xyz, target, offsets, flags, reps) -> dict:
+    out = Tuning()
+    _check(load().srn_autotune(h, stream, xyz, target, _i64(offsets), flags, reps, ct.byref(out)))
+    return {f: getattr(out, f) for f, _ in Tuning._fields_}
 
 
 def srn_get_status(h, stream) -> None:
