@@ -248,6 +248,22 @@ typedef struct {
 srn_status srn_set_schedule(srn_handle* h, const srn_schedule* sched);
 srn_status srn_read_schedule(srn_handle* h, void* stream, srn_brick_schedule* out_host);
 
+/* Batch shares after bricks finish (Sec. 5.2: a finished model frees its GPU for the next
+ * one; here the bricks share one GPU, and a finished brick frees its share of each
+ * batch for the bricks still training).  Host only; no handle, no GPU.
+ * base_counts[n_bricks] (each >= 1) are the points per brick while all train; state is
+ * srn_read_schedule's output (only `finished` is read).  out_offsets[n_bricks + 1]
+ * receives batch offsets with the same total: a finished brick keeps
+ * min(min_points, base) points (min_points >= 1, so its L_rec stays defined), and the
+ * points the finished bricks give up, P, go to the unfinished bricks in proportion to
+ * their base counts: brick a gets floor(P base_a / W) more (W = the unfinished bricks'
+ * base total), and the points that flooring leaves go one each to the unfinished bricks
+ * with the largest remainders (P base_a mod W), ties to the lower index.  With no
+ * brick finished, or every brick finished, the offsets are those of the base counts.
+ * Passing the new offsets to srn_train_step captures a new CUDA graph for them. */
+srn_status srn_rebalance(int32_t n_bricks, const int64_t* base_counts, const srn_brick_schedule* state,
+                         int64_t min_points, int64_t* out_offsets);
+
 /* Headless volume render (Sec. 6) of the domain decomposition (Sec. 5.3) into
  * rgba_dev [height][width][4].  Each ray is clipped to [-1,1]^3 and sampled at
  * `samples` midpoints; every sample is hashed to its brick (grid[3] = I, J, K,

@@ -763,6 +763,51 @@ srn_status srn_read_schedule(srn_handle* h, void* stream, srn_brick_schedule* ou
   return SRN_OK;
 }
 
+srn_status srn_rebalance(int32_t n_bricks, const int64_t* base, const srn_brick_schedule* state,
+                         int64_t min_points, int64_t* out) {
+  if (n_bricks < 1 || n_bricks > SRN_MAX_BRICKS)
+    return fail(SRN_ERR_INVALID_ARG, "n_bricks %d outside [1, %d]", (int)n_bricks, SRN_MAX_BRICKS);
+  if (!base || !state || !out) return fail(SRN_ERR_INVALID_ARG, "NULL argument");
+  if (min_points < 1) return fail(SRN_ERR_INVALID_ARG, "min_points must be >= 1");
+  const int64_t kCap = (int64_t)1 << 56;   // keeps every sum and product below 2^120
+  int64_t total = 0, freed = 0, w = 0;
+  int n_done = 0;
+  for (int b = 0; b < n_bricks; ++b) {
+    if (base[b] < 1 || base[b] > kCap) return fail(SRN_ERR_INVALID_ARG, "base count of brick %d out of range", b);
+    total += base[b];
+    if (total > kCap) return fail(SRN_ERR_INVALID_ARG, "base counts sum beyond 2^56");
+    if (state[b].finished) {
+      freed += base[b] - std::min(min_points, base[b]);
+      ++n_done;
+    } else {
+      w += base[b];
+    }
+  }
+  std::vector<int64_t> cnt(base, base + n_bricks);
+  if (n_done > 0 && n_done < n_bricks) {
+    std::vector<std::pair<int64_t, int>> rem;   // (remainder, brick) of the unfinished bricks
+    int64_t given = 0;
+    for (int b = 0; b < n_bricks; ++b) {
+      if (state[b].finished) {
+        cnt[b] = std::min(min_points, base[b]);
+        continue;
+      }
+      const unsigned __int128 q = (unsigned __int128)freed * (unsigned __int128)base[b];
+      const int64_t more = (int64_t)(q / (unsigned __int128)w);
+      cnt[b] += more;
+      given += more;
+      rem.emplace_back((int64_t)(q % (unsigned __int128)w), b);
+    }
+    std::stable_sort(rem.begin(), rem.end(), [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) {
+      return x.first > y.first;
+    });
+    for (int64_t k = 0; k < freed - given; ++k) cnt[rem[(size_t)k].second] += 1;
+  }
+  out[0] = 0;
+  for (int b = 0; b < n_bricks; ++b) out[b + 1] = out[b] + cnt[b];
+  return SRN_OK;
+}
+
 srn_status srn_save_state(srn_handle* h, void* stream, void* dst, size_t bytes) {
   srn_status s = check_handle(h);
   if (s != SRN_OK) return s;

@@ -162,6 +162,11 @@ class SRN:
     def read_schedule(self, stream=None) -> list:
         return _s.srn_read_schedule(self.handle, _stream_ptr(stream), self.n_bricks)
 
+    def rebalanced_offsets(self, base_counts, min_points: int = 1024, stream=None) -> list:
+        """Batch offsets that give the finished bricks' shares to the bricks still
+        training (srn_rebalance on the device routine's state; synchronises `stream`)."""
+        return _s.srn_rebalance(base_counts, self.read_schedule(stream), min_points)
+
     def train_step(self, seed, volume, boxes, offsets, density, xyz, target, stream=None, schedule=False):
         dims = [volume.shape[2], volume.shape[1], volume.shape[0]]
         flags = _s.SRN_SCHEDULE if schedule else (_s.SRN_DENSITY if density else 0)

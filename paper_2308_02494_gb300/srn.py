@@ -36,7 +36,7 @@ EXPORTS = (
     "srn_step", "srn_train_step", "srn_render", "srn_set_timing", "srn_read_timing", "srn_get_status",
     "srn_sample_points_static", "srn_decode", "srn_state_bytes", "srn_save_state", "srn_load_state",
     "srn_set_schedule", "srn_read_schedule", "srn_render_progressive", "srn_get_tuning", "srn_set_tuning",
-    "srn_autotune",
+    "srn_autotune", "srn_rebalance",
 )
 SRN_STATIC_SAMPLER_MAX_POINTS = 131072
 SRN_STATIC_SAMPLER_MAX_BRICKS = 8
@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
         "srn_get_tuning": [P, ct.POINTER(Tuning)],
         "srn_set_tuning": [P, ct.POINTER(Tuning)],
         "srn_autotune": [P, P, P, P, I64P, U32, I32, ct.POINTER(Tuning)],
+        "srn_rebalance": [I32, I64P, ct.POINTER(BrickSchedule), I64, I64P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -251,6 +252,18 @@ def srn_read_schedule(h, stream, n_bricks: int) -> list:
     out = (BrickSchedule * n_bricks)()
     _check(load().srn_read_schedule(h, stream, out))
     return [{f: getattr(o, f) for f, _ in BrickSchedule._fields_} for o in out]
+
+
+def srn_rebalance(base_counts, finished, min_points) -> list:
+    """Batch offsets after bricks finish; `finished` is one flag per brick (or
+    srn_read_schedule's dicts)."""
+    n = len(base_counts)
+    st = (BrickSchedule * n)()
+    for b, f in enumerate(finished):
+        st[b].finished = int(f["finished"] if isinstance(f, dict) else f)
+    out = (ct.c_int64 * (n + 1))()
+    _check(load().srn_rebalance(n, _i64(base_counts), st, int(min_points), out))
+    return list(out)
 
 
 def srn_state_bytes(h) -> int:

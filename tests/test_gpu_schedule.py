@@ -88,3 +88,50 @@ def test_schedule_flag_needs_a_routine():
                      schedule=True)
     with pytest.raises(S.SrnError):
         m.set_schedule(density_window=5000)
+
+
+def test_finished_bricks_give_their_share_to_the_others():
+    """After a brick finishes, srn_rebalance moves its share of the batch to the bricks
+    still training; the next steps run on the new offsets (a new CUDA graph), the finished
+    brick keeps its minimum share and stays frozen."""
+    import torch
+    from paper_2308_02494_gb300 import srn as S
+    m = _model("bf16")
+    r = ROUTINE
+    m.set_schedule(delay_iters=r["delay"], density_window=r["window"], density_rel=r["rel"],
+                   density_frac=r["frac"], total_iters=r["total"], plateau_window=r["pwin"],
+                   plateau_rel=r["prel"], plateau_factor=r["pfactor"], plateau_max=r["pmax"])
+    base = [600, 400]
+    off = [0, 600, 1000]
+    vol_np, _ = synth.gaussian_volume(32, 16, seed=3)
+    vol = torch.as_tensor(np.asarray(vol_np, dtype=np.float32), device="cuda")
+    boxes = synth.brick_boxes(32, (2, 1, 1), ghost=1)
+    xyz = torch.empty((1000, 3), dtype=torch.float32, device="cuda")
+    tgt = torch.empty(1000, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    state = m.read_schedule()
+    for _ in range(r["total"]):
+        with torch.cuda.stream(stream):
+            m.train_step(7, vol, boxes, off, True, xyz, tgt, stream=stream, schedule=True)
+        state = m.read_schedule(stream)
+        if any(s["finished"] for s in state):
+            break
+    fin = [bool(s["finished"]) for s in state]
+    assert any(fin)
+    new = m.rebalanced_offsets(base, min_points=64, stream=stream)
+    assert new == S.srn_rebalance(base, fin, 64) and new[-1] == 1000
+    if not all(fin):
+        for b in range(2):
+            assert (new[b + 1] - new[b] == 64) if fin[b] else (new[b + 1] - new[b] > base[b])
+    frozen = [{k: v.clone() for k, v in m._views(m.params, b).items()} for b in range(2)]
+    for _ in range(3):   # eager, capture, replay of the new offsets' graph
+        with torch.cuda.stream(stream):
+            m.train_step(7, vol, boxes, new, True, xyz, tgt, stream=stream, schedule=True)
+    stream.synchronize()
+    m.status(stream)
+    losses = m.losses.cpu().numpy()
+    assert list(losses[:, 3]) == [new[1] - new[0], new[2] - new[1]]   # points per brick
+    for b in range(2):
+        after = m._views(m.params, b)
+        moved = not torch.equal(frozen[b]["F"], after["F"])
+        assert moved == (not fin[b]), b
