@@ -1,6 +1,7 @@
 // libsrn kernels around the fused query:
-//   * density loss passes 2 and 3 (Eq. 8, Eq. 9 and dL_den/dG) and the per-brick
-//     finalisation (losses, dG from the float64 sums);
+//   * the density loss: rho per point (Eq. 7) for the BF16 pass, passes 2 and 3
+//     (Eq. 8, Eq. 9 and dL_den/dG) and the per-brick finalisation (losses, dG from
+//     the float64 sums);
 //   * Adam (Sec. 6) over the flat parameter buffer, plus the BF16 shadow refresh;
 //   * the batch sampler (Philox4x32-10, then a counting sort by 32^3 Morton bin);
 //   * the ground-truth lookup v(x) of Sec. 4.3.1 (trilinear in a float32 volume).
