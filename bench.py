@@ -126,46 +126,54 @@ x = synth.uniform_points(n, 1).astype(np.float64)
 vol, _ = synth.gaussian_volume(64, 16, seed=0)
 keys = ("F", "W1", "W2", "w3", "G")
 mom = {k: (np.zeros_like(p[k]), np.zeros_like(p[k])) for k in keys}
-t0 = time.perf_counter(); done = 0; reps = 0
-while True:
-    v = ap.volume_sample(vol, x)
-    g = ap.grad_rec(p, x, v)
-    d = ap.grad_density(p["G"], x, g["h"])
-    grads = {"F": g["dF"], "W1": g["dW1"], "W2": g["dW2"], "w3": g["dw3"], "G": d["dG"]}
-    for k in keys:
-        lr = 1e-3 if k == "G" else 1e-2
-        p[k], m1, m2 = ap.adam_update(p[k], grads[k], mom[k][0], mom[k][1], reps + 1, lr)
-        mom[k] = (m1, m2)
-    done += n; reps += 1
-    if time.perf_counter() - t0 >= %(budget)f:
-        break
-print(json.dumps({"points": done, "seconds": time.perf_counter() - t0, "reps": reps}))
+it = 0
+out = []
+for step in range(%(steps)d):   # each step: whole iterations until its time budget is spent
+    t0 = time.perf_counter(); done = 0; reps = 0
+    while True:
+        v = ap.volume_sample(vol, x)
+        g = ap.grad_rec(p, x, v)
+        d = ap.grad_density(p["G"], x, g["h"])
+        grads = {"F": g["dF"], "W1": g["dW1"], "W2": g["dW2"], "w3": g["dw3"], "G": d["dG"]}
+        it += 1
+        for k in keys:
+            lr = 1e-3 if k == "G" else 1e-2
+            p[k], m1, m2 = ap.adam_update(p[k], grads[k], mom[k][0], mom[k][1], it, lr)
+            mom[k] = (m1, m2)
+        done += n; reps += 1
+        if time.perf_counter() - t0 >= %(budget)f:
+            break
+    out.append({"points": done, "seconds": time.perf_counter() - t0, "reps": reps})
+print(json.dumps(out))
 """
 
 
-def oracle_rate(budget_s: float, n: int = 2048):
+def oracle_rate(budget_s: float, n: int = 2048, steps: int = 1, warmup: int = 0):
+    """The FP64 oracle's training-iteration rate on one host thread, in one subprocess:
+    `warmup` untimed then `steps` timed steps of at least budget_s seconds each (whole
+    iterations).  Returns (points/s over the timed steps, per-step points/s, a
+    description of the sample)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET % {"root": ROOT, "n": n, "budget": budget_s}
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    code = ORACLE_SNIPPET % {"root": ROOT, "n": n, "budget": budget_s, "steps": warmup + steps}
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=600 + 2 * (warmup + steps) * budget_s)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
-    r = json.loads(out.stdout.strip().splitlines()[-1])
+    r = json.loads(out.stdout.strip().splitlines()[-1])[warmup:]
+    points, seconds, reps = (sum(q[k] for q in r) for k in ("points", "seconds", "reps"))
     sample = (f"FP64 oracle, 1 thread: one brick's model (M=64, R=32, C=2, 128->64->64->1), "
-              f"{n}-point batches x {r['reps']} reps: target lookup + fwd + L_rec bwd + density bwd + "
-              f"Adam over all 4.2M parameters, {r['seconds']:.1f} s")
-    return r["points"] / r["seconds"], sample
+              f"{n}-point batches x {reps} reps: target lookup + fwd + L_rec bwd + density bwd + "
+              f"Adam over all 4.2M parameters, {seconds:.1f} s")
+    return points / seconds, [q["points"] / q["seconds"] for q in r], sample
 
 
 def run_reference(args, workload):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    rates = []
-    budget = max(1.0, args.cpu_seconds / max(1, args.steps))
-    for _ in range(max(1, args.steps)):
-        rate, sample = oracle_rate(budget)
-        rates.append(rate)
-    value = sum(rates) / len(rates)
+    # every step a bounded sample (at least one whole iteration), all in one process
+    steps = max(1, args.steps)
+    value, _, sample = oracle_rate(max(0.2, args.cpu_seconds / steps), steps=steps, warmup=max(0, args.warmup))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -469,7 +477,7 @@ def run_own(args, workload):
         return
     cpu = None
     if world == 1:
-        rate, sample = oracle_rate(args.cpu_seconds)
+        rate, _, sample = oracle_rate(args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     cfg = dict(wl)
     cfg["points_per_step"] = points_all // args.steps
