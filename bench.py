@@ -58,6 +58,38 @@ def measured_traffic(name):
     return NCU_TRAFFIC.get(name) if h.hexdigest() == NCU_TRAFFIC["sources_sha1"] else None
 
 
+# On-chip rates for the gather and the scatter, whose per-(point, grid) corner work
+# lives in shared memory: the scatter adds 8 x C contributions with conflict-free
+# red.shared.add.u32 (measured on this GB300 with a probe of 16 warps per SM,
+# conflict-free addresses: 0.94 warp instructions per SM clock); the encoder reads 8
+# corners of C bf16 (one 4-byte word for C = 2) with conflict-free shared loads
+# (nominal: one warp instruction of 32 x 4 B per SM clock).
+SMEM_RED_PER_CLK = 0.94
+SMEM_LDS_PER_CLK = 1.0
+
+
+def onchip_rooflines(wl, n_total, kt, sms, sm_mhz):
+    """Shared-memory instruction rooflines of k_scat and k_enc (warp instructions/s)."""
+    m, c = wl["grids"], wl["channels"]
+    work = {"k_scat": (n_total * m * 8 * c / 32, SMEM_RED_PER_CLK,
+                       "8 corners x C channels per (point, grid), one lane each: shared integer reductions",
+                       "measured red.shared.add.u32 rate, conflict-free"),
+            "k_enc": (n_total * m * 8 / 32, SMEM_LDS_PER_CLK,
+                      "8 corners per (point, grid), one lane each: shared loads of C bf16",
+                      "nominal shared-load issue rate, conflict-free")}
+    out = {}
+    for name, (inst, per_clk, per, psrc) in work.items():
+        ms = kt.get(name)
+        if not ms:
+            continue
+        ach = inst / (ms / 1e3) / 1e9
+        peak = per_clk * sms * sm_mhz * 1e6 / 1e9
+        out[name] = {"bound": "smem", "achieved": ach, "peak": peak, "unit": "G warp instructions/s",
+                     "frac": ach / peak, "algorithmic": per, "algorithmic_per_launch": inst,
+                     "peak_source": f"{psrc}, {per_clk} per SM clock x {sms} SMs x {sm_mhz:.0f} MHz"}
+    return out
+
+
 def kernel_rooflines(wl, n_total, kt, hbm, tf_sus, src):
     """Roofline entries of the training-pass kernels from their measured mean times (ms)."""
     m, r, c = wl["grids"], wl["res"], wl["channels"]
@@ -421,6 +453,10 @@ def run_own(args, workload):
         roof = dict(rl[dom], kernel=dom, query_pass_ms=kt["query"],
                     others={k: {f: v[f] for f in ("bound", "achieved", "unit", "frac", "kernel_ms")}
                             for k, v in rl.items() if k != dom})
+        # the gather's and the scatter's shared-memory work against its instruction rate,
+        # at the highest SM clock seen (nominal 2070 MHz without a clock record)
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        roof["onchip"] = onchip_rooflines(wl, n_total, kt, sms, clk.get("sm_max_mhz") or 2070.0)
     else:
         fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
         ach = FLOP_PER_POINT * n_total / (kt["query"] / 1e3) / 1e12
