@@ -104,6 +104,34 @@ def test_ortho_centre_ray_length_and_misses():
     assert np.all(img == 0.0)
 
 
+def test_perspective_render_of_a_constant_field_depends_only_on_each_chord():
+    # Perspective rays all leave the eye.  With a constant field every sample has the
+    # same alpha, and n samples of a chord L give 1 - prod(1 - alpha) = 1 - exp(-a L /
+    # dt_ref) whatever n is.  The camera on the z axis at distance 3 sends its centre
+    # ray through the box on the axis (in at t = 2, out at t = 4), and the image of this
+    # mirror-symmetric scene is mirror-symmetric.
+    cam = synth.orbit_camera(0.0, 0.0, ortho=False)
+    W = H = 5
+    org, d = orr.camera_rays(cam, W, H)
+    np.testing.assert_allclose(org, np.broadcast_to(cam["eye"], org.shape), atol=0)
+    np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-12)
+    centre = (H // 2) * W + W // 2
+    np.testing.assert_allclose(d[centre], cam["forward"], atol=1e-7)
+    t0, t1, hit = orr.box_interval(org, d)
+    assert hit[centre]
+    np.testing.assert_allclose([t0[centre], t1[centre]], [2.0, 4.0], atol=1e-6)
+    lut = np.zeros((256, 4), dtype=np.float32)
+    lut[0] = [0.3, 0.6, 0.1, 0.004]
+    a = float(lut[0, 3])
+    for n in (7, 32):
+        img = orr.render([_zero_model()], [[0, 0, 0, 8, 8, 8]], (1, 1, 1), 9, cam, lut, 0.0, 1.0, W, H, n)
+        want = np.where(hit, 1.0 - np.exp(-a * (t1 - t0) / orr.DT_REF), 0.0).reshape(H, W)
+        np.testing.assert_allclose(img[..., 3], want, rtol=1e-9, atol=1e-15)
+        np.testing.assert_allclose(img[..., 1], float(lut[0, 1]) * want, rtol=1e-9, atol=1e-15)
+        np.testing.assert_allclose(img, img[:, ::-1], atol=1e-12)
+        np.testing.assert_allclose(img, img[::-1, :], atol=1e-12)
+
+
 def test_lut_linear_interpolation():
     lut = np.zeros((256, 4))
     lut[:, 0] = np.arange(256) / 255.0
