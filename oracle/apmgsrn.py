@@ -219,9 +219,11 @@ def grad_rec(params: dict, x, v, rnd=None):
 
     Chain rule written out: f = m (max-min) + min, dL/df = 2 (f - v)/N.
     rnd (see mlp_forward) also rounds the activation-side operand of every
-    backward matrix product (dz2, dz1, and the y / ReLU(z1) factors of dW).
-    Returns dict(L_rec, f, h, dF, dW1, dW2, dw3, dy) where h = (f - v)^2 per point
-    and dy = dL/dy [N, M*C]."""
+    backward matrix product (dz2, dz1, and the y / ReLU(z1) factors of dW) and
+    dL/dy itself, which the mixed-precision reading hands on to the adjoint of
+    Eq. 2 in that format.  The ReLU masks are taken from the unrounded
+    pre-activations.  Returns dict(L_rec, f, h, dF, dW1, dW2, dw3, dy) where
+    h = (f - v)^2 per point and dy = dL/dy [N, M*C]."""
     q = rnd or _ident
     F = np.asarray(params["F"], dtype=np.float64)
     G = np.asarray(params["G"], dtype=np.float64)
@@ -243,7 +245,7 @@ def grad_rec(params: dict, x, v, rnd=None):
     dW2 = dz2.T @ c["h1q"]
     dz1 = q((dz2 @ W2) * (c["z1"] > 0))
     dW1 = dz1.T @ c["yq"]
-    dy = dz1 @ W1                                     # [N, M*C]
+    dy = q(dz1 @ W1)                                  # [N, M*C]
     dF = np.zeros_like(F)
     u = local_coords(G, x)
     for i in range(M):
