@@ -155,7 +155,12 @@ srn_status srn_sample_points(srn_handle* h, void* stream, uint64_t seed, uint64_
  *   - Same draws and same per-brick Morton ordering as srn_sample_points with
  *     step_dev = NULL (order inside a bin may differ between runs).
  *   - The first call on a device looks up that device's copy of the array (with the
- *     device current); make that first call before any stream capture.
+ *     device current); make that first call before any stream capture.  The address
+ *     is kept per device index for the rest of the process: it belongs to the CUDA
+ *     runtime's primary context of that device, so calls must run with that context
+ *     current (a caller's own driver-API context on the same device is not
+ *     supported), and after cudaDeviceReset the kept address is stale -- do not call
+ *     this entry point again in that process.
  *   - All calls share the one array: calls that overlap on the GPU (two streams, or two
  *     host threads) race on it and must be serialised by the caller.  The histograms
  *     are cleared on the stream at the start of every call. */

@@ -1094,6 +1094,18 @@ srn_status srn_set_tuning(srn_handle* h, const srn_tuning* t) {
   return SRN_OK;
 }
 
+namespace {
+// Reads the device status word into *v and clears it (synchronises the stream).
+srn_status take_status(srn_handle* h, cudaStream_t cs, int32_t* v) {
+  *v = 0;
+  cudaError_t e = cudaMemcpyAsync(v, h->status(), sizeof *v, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e == cudaSuccess && *v) e = cudaMemsetAsync(h->status(), 0, sizeof *v, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "status read");
+}
+}  // namespace
+
 srn_status srn_autotune(srn_handle* h, void* stream, const float* xyz, const float* target,
                         const int64_t* offsets, uint32_t flags, int32_t reps, srn_tuning* out) {
   srn_status s = check_handle(h);
@@ -1128,13 +1140,25 @@ srn_status srn_autotune(srn_handle* h, void* stream, const float* xyz, const flo
   const srn::Tuning start = h->tune;
   srn::Tuning best = start;
   float best_ms = 0.f;
-  s = time_backward(h, stream, xyz, target, br, flags, reps, t0, t1, &best_ms);
+  // A pass whose decoder gave up on a tensor-core wait returns early and would look
+  // fast: the status word is read (and cleared) after every timed shape, and a shape
+  // that set the timeout bit is dropped.  Bits set before the call are put back.
+  int32_t pre = 0, st = 0;
+  s = take_status(h, cs, &pre);
+  if (s == SRN_OK) s = time_backward(h, stream, xyz, target, br, flags, reps, t0, t1, &best_ms);
+  if (s == SRN_OK) s = take_status(h, cs, &st);
+  pre |= st & 1;
+  if (s == SRN_OK && (st & 2))
+    s = fail(SRN_ERR_DEVICE_TIMEOUT, "srn_autotune: the current tile shape gave up waiting for the tensor cores");
   for (int tp : kPoints) {
     for (int lv : kLevels) {
       if (s != SRN_OK || (tp == start.tile_points && lv == start.tile_level)) continue;
       h->tune = srn::Tuning{tp, lv, start.density_ctas};
       float ms = 0.f;
       if ((s = time_backward(h, stream, xyz, target, br, flags, reps, t0, t1, &ms)) != SRN_OK) break;
+      if ((s = take_status(h, cs, &st)) != SRN_OK) break;
+      pre |= st & 1;
+      if (st & 2) continue;   // gave up: not a candidate
       if (ms < 0.99f * best_ms) {
         best = h->tune;
         best_ms = ms;
@@ -1143,6 +1167,9 @@ srn_status srn_autotune(srn_handle* h, void* stream, const float* xyz, const flo
   }
   h->tune = start;
   h->timing = timing;
+  if (pre && (e = cudaMemcpyAsync(h->status(), &pre, sizeof pre, cudaMemcpyHostToDevice, cs)) == cudaSuccess)
+    e = cudaStreamSynchronize(cs);
+  if (pre && e != cudaSuccess && s == SRN_OK) s = cuda_fail(e, "status restore");
   if (s == SRN_OK) {
     install_tuning(h, best);
     s = do_backward(h, stream, xyz, target, br, flags, nullptr);

@@ -25,6 +25,8 @@ unsigned char* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of this device's copy of the array (looked up once per device, with
 // that device current; host code cannot use the array's name as a device address).
+// The address is that of the runtime's primary context and is never looked up again:
+// it does not follow a caller's own driver-API context, nor a cudaDeviceReset.
 srn_status scratch_for_current_device(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

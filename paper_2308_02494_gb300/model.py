@@ -74,19 +74,33 @@ class SRN:
             "G": flat[L.off_G + b * L.size_G: L.off_G + b * L.size_G + M * 12].view(M, 3, 4),
         }
 
+    def pack(self, models) -> torch.Tensor:
+        """A new flat float32 parameter tensor (the library's layout) holding one dict
+        per brick (F, G, W1, W2, w3 as numpy arrays); padding entries are zero."""
+        if isinstance(models, dict):
+            models = [models]
+        assert len(models) == self.n_bricks
+        flat = torch.zeros_like(self.params)
+        for b, m in enumerate(models):
+            v = self._views(flat, b)
+            for k in ("F", "W1", "W2", "w3", "G"):
+                v[k].copy_(torch.as_tensor(np.asarray(m[k], dtype=np.float32)))
+        return flat
+
     def set_params(self, models, stream=None) -> None:
         """models: one dict per brick (F, G, W1, W2, w3, vmin, vmax) of numpy arrays."""
         if isinstance(models, dict):
             models = [models]
-        assert len(models) == self.n_bricks
+        self.params.copy_(self.pack(models))
         for b, m in enumerate(models):
-            v = self._views(self.params, b)
-            for k in ("F", "W1", "W2", "w3", "G"):
-                v[k].copy_(torch.as_tensor(np.asarray(m[k], dtype=np.float32)))
             self.range[b, 0] = float(m["vmin"])
             self.range[b, 1] = float(m["vmax"])
         self.adam_m.zero_()
         self.adam_v.zero_()
+        self.sync_shadow(stream)
+
+    def sync_shadow(self, stream=None) -> None:
+        """Re-derive the BF16 shadow from the float32 parameters (srn_sync_shadow)."""
         _s.srn_sync_shadow(self.handle, _stream_ptr(stream))
 
     def get(self, which: str = "params") -> list:
@@ -239,6 +253,13 @@ def ct_f3(v):
 class APMGSRNFunction(torch.autograd.Function):
     """f = APMGSRN(x) with the flat parameter tensor as the differentiable input.
 
+    ``params`` is a float32 tensor in the model's flat layout (``model.params``
+    itself, a clone of it, or ``model.pack(...)``).  The library evaluates the
+    model held by its handle, so forward first makes the model hold ``params``:
+    unless ``params`` is ``model.params`` itself, its values are copied into
+    ``model.params`` and the BF16 shadow is re-derived.  The model keeps those
+    values afterwards, and backward differentiates at them.
+
     forward runs ``srn_forward``; backward runs ``srn_backward`` with
     ``SRN_UPSTREAM`` (the incoming dL/df per point) and returns the flat
     gradient for the parameters (no gradient for the coordinates).  With
@@ -248,6 +269,12 @@ class APMGSRNFunction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, xyz, params, model: SRN, offsets, grad_transforms: bool = False):
+        if params.shape != model.params.shape or params.dtype != torch.float32 or params.device != model.params.device:
+            raise ValueError(f"params must be a float32 tensor of shape {tuple(model.params.shape)} on "
+                             f"{model.params.device} (the model's flat layout)")
+        if params.data_ptr() != model.params.data_ptr():
+            model.params.copy_(params.detach())
+            model.sync_shadow()
         ctx.model, ctx.offsets, ctx.rec_dg = model, offsets, grad_transforms
         ctx.save_for_backward(xyz)
         return model.forward(xyz, offsets)

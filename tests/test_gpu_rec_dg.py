@@ -36,11 +36,9 @@ def _points(params, n, seed, rnd, dense=False, margin=2e-4):
 def _want(params, x, v, precision):
     """Oracle dG through the features, and its summation scale: the same sum with
     every term replaced by its absolute value (float summation errs relative to it).
-    The BF16 path feeds the kernels dL/dy rounded to bfloat16, as it stores it."""
+    On the BF16 path the oracle's dL/dy is rounded to bfloat16, as the kernels store it."""
     g = ap.grad_rec(params, x.astype(np.float64), v.astype(np.float64), rnd=RND[precision])
     dy = g["dy"]
-    if precision == "bf16":
-        dy = ap.bf16(dy)
     want = ap.grad_transform_through_features(params, x, dy)
     xt = np.concatenate([np.abs(x.astype(np.float64)), np.ones((len(x), 1))], axis=1)
     u = ap.local_coords(params["G"], x.astype(np.float64))
@@ -119,3 +117,36 @@ def test_autograd_with_transforms_equals_the_mse_backward_with_rec_dg(precision,
     gA, gM = g_auto[L.off_G:L.off_G + L.size_G], g_mse[L.off_G:L.off_G + L.size_G]
     assert torch.linalg.norm(gM) > 0
     assert torch.linalg.norm(gA - gM) <= 5 * TOL[precision] * torch.linalg.norm(gM)
+
+
+@pytest.mark.parametrize("precision,shape", [("fp32", "m8r16c2"), ("bf16", "m64r32c2")])
+def test_autograd_function_differentiates_at_its_params_input(precision, shape):
+    # The model is created with one parameter set; the function is given another (only
+    # as its input).  f and every gradient must be the oracle's at the input's values.
+    import torch
+    from paper_2308_02494_gb300 import synth
+    from gpu_util import as_stored, rel_l2
+    from paper_2308_02494_gb300.model import APMGSRNFunction
+    n = 900
+    m, ref_a = make_model(SHAPES[shape], 1, precision, 2048, seed=61)
+    other = synth.parity_model(SHAPES[shape], 62, shrink=0.4)
+    other["vmin"], other["vmax"] = ref_a[0]["vmin"], ref_a[0]["vmax"]   # the range is not a parameter
+    ref_b = as_stored(other, precision)
+    x = _points(ref_b, n, 63, RND[precision])
+    v = np.random.default_rng(64).uniform(-0.5, 1.5, n).astype(np.float32)
+    xt, vt = torch.as_tensor(x, device="cuda"), torch.as_tensor(v, device="cuda")
+    params = m.pack(other).requires_grad_(True)
+    assert not torch.equal(params.detach(), m.params)
+    f = APMGSRNFunction.apply(xt, params, m, [0, n], True)
+    ((f - vt) ** 2).mean().backward()
+    want, scale, g = _want(ref_b, x, v, precision)
+    assert rel_l2(f.detach().cpu().numpy(), g["f"]) <= TOL[precision]
+    got = m._views(params.grad, 0)
+    for k, w in (("F", "dF"), ("W1", "dW1"), ("W2", "dW2"), ("w3", "dw3")):
+        e = rel_l2(got[k].cpu().numpy(), g[w])
+        assert e <= TOL[precision], (k, e)
+    assert _err(got["G"].cpu().numpy(), want, scale) <= TOL[precision]
+    # the model now holds the input's values (and its BF16 shadow follows them)
+    assert torch.equal(m.params, params.detach())
+    with pytest.raises(ValueError):
+        APMGSRNFunction.apply(xt, params.detach()[:-1], m, [0, n])

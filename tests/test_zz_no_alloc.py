@@ -9,6 +9,7 @@ if it fails, a run that stops at the first failure has already run every other t
 import numpy as np
 import pytest
 
+from oracle import sampler as osp
 from paper_2308_02494_gb300 import srn as S
 from paper_2308_02494_gb300 import synth
 from gpu_util import ensure_built, make_model
@@ -44,6 +45,8 @@ def test_static_sampler_matches_the_workspace_sampler_on_two_calls_in_a_row():
         for b in range(4):
             g, w = got[off[b]:off[b + 1]], want[off[b]:off[b + 1]]
             np.testing.assert_array_equal(_as_set(g), _as_set(w))   # same draws
+            # and the draws are the published Philox4x32-10 ones of the oracle's sampler
+            np.testing.assert_array_equal(_as_set(g), _as_set(osp.sample_points(seed, step, b, counts[b])))
             if len(g):
                 assert np.all(np.diff(_morton(g)) >= 0)                # same bin order
 
