@@ -75,11 +75,12 @@ def lut_lookup(lut, s):
     return lut[i0] * (1.0 - fr) + lut[i0 + 1] * fr
 
 
-def dd_query(models, boxes, grid, vox: int, p):
+def dd_query(models, boxes, grid, vox: int, p, rnd=None):
     """Query a domain-decomposed set of models at global points p [N, 3]:
     the Sec. 5.3 hash picks the brick, p is mapped into that brick's local
     domain, and that brick's model answers.  A single model is the case
-    grid = (1, 1, 1) with the whole volume as its box."""
+    grid = (1, 1, 1) with the whole volume as its box.  rnd is the decoder's
+    operand rounding (see apmgsrn.mlp_forward)."""
     p = np.asarray(p, dtype=np.float64)
     b = ap.brick_index(p, grid)
     out = np.zeros(p.shape[0])
@@ -87,13 +88,14 @@ def dd_query(models, boxes, grid, vox: int, p):
         sel = b == k
         if np.any(sel):
             loc = ap.global_to_brick_local(p[sel], boxes[k], vox)
-            out[sel] = ap.query(params, loc)
+            out[sel] = ap.query(params, loc, rnd)
     return out
 
 
 def render(models, boxes, grid, vox, cam, lut, vmin, vmax, width, height, n_samples,
-           pixels=None):
-    """RGBA image [H, W, 4] (or [len(pixels), 4] for a list of flat pixel indices)."""
+           pixels=None, rnd=None):
+    """RGBA image [H, W, 4] (or [len(pixels), 4] for a list of flat pixel indices);
+    rnd as in dd_query."""
     org, d = camera_rays(cam, width, height)
     if pixels is not None:
         org, d = org[pixels], d[pixels]
@@ -106,7 +108,7 @@ def render(models, boxes, grid, vox, cam, lut, vmin, vmax, width, height, n_samp
     for j in range(n_samples):
         t = t0[rays] + (j + 0.5) * dt[rays]
         p = org[rays] + t[:, None] * d[rays]
-        f = dd_query(models, boxes, grid, vox, p)
+        f = dd_query(models, boxes, grid, vox, p, rnd)
         rgba = lut_lookup(lut, (f - vmin) / (vmax - vmin))
         alpha = 1.0 - np.exp(-rgba[:, 3] * dt[rays] / DT_REF)
         color[rays] += (trans[rays] * alpha)[:, None] * rgba[:, :3]

@@ -79,9 +79,9 @@ def dG_error(got, want, scale) -> float:
     return float(np.max(np.abs(np.asarray(got) - want) / (scale + 1e-300)))
 
 
-def morton_sorted(x, bits=5):
-    """x reordered by the Morton code of its 2^bits-per-axis bin (the order the
-    library's sampler produces), stable inside a bin."""
+def morton_order(x, bits=5):
+    """Permutation that orders x by the Morton code of its 2^bits-per-axis bin (the
+    order the library's sampler produces), stable inside a bin."""
     x = np.asarray(x)
     cell = np.minimum(((x.astype(np.float64) + 1.0) * (1 << bits) / 2.0).astype(np.int64), (1 << bits) - 1)
     cell = np.maximum(cell, 0)
@@ -89,7 +89,25 @@ def morton_sorted(x, bits=5):
     for bit in range(bits):
         for a in range(3):
             code |= ((cell[:, a] >> bit) & 1) << (3 * bit + a)
-    return x[np.argsort(code, kind="stable")]
+    return np.argsort(code, kind="stable")
+
+
+def morton_sorted(x, bits=5):
+    """x in the order of morton_order."""
+    x = np.asarray(x)
+    return x[morton_order(x, bits)]
+
+
+def near_bf16_midpoint(a, eps, min_ulp=3e-5):
+    """Entries of a within eps (absolute, broadcast) of a bfloat16 rounding midpoint,
+    among those whose bfloat16 spacing is at least min_ulp (a one-step change of a
+    smaller entry moves nothing downstream by more than min_ulp times its weight)."""
+    a = np.abs(np.asarray(a, dtype=np.float64))
+    e = np.floor(np.log2(np.maximum(a, 1e-300)))
+    ulp = np.exp2(e - 7)                      # 8 significant bits
+    q = a / ulp
+    dist = np.abs(q - np.floor(q) - 0.5) * ulp
+    return (dist < eps) & (ulp >= min_ulp) & (a > 0)
 
 
 def points_off_kinks(params, x, rnd, margin=2e-3):
@@ -105,6 +123,24 @@ def points_off_kinks(params, x, rnd, margin=2e-3):
         rms = np.sqrt(np.mean(z * z)) + 1e-30
         ok &= np.all(np.abs(z) > margin * rms, axis=1)
     return np.asarray(x)[ok]
+
+
+def points_off_bf16_midpoints(params, x):
+    """Keep the points whose BF16 operand roundings are the same in float32 and float64:
+    no feature y and no ReLU(z1) lies within the float32 error of its computation (the
+    8-corner blend, ~2^-22 of the largest feature; the K-term dot product, ~4e-7 of its
+    absolute terms) of a bfloat16 rounding midpoint, where the kernel (rounding a float32
+    value) and the oracle (rounding a float64 value) would pick neighbouring bfloat16
+    numbers.  Such a one-step change of an operand of 2^-8 relative size moves f by up
+    to ~1e-3 and, through dL/dm, that point's whole gradient."""
+    x = np.asarray(x)
+    y = ap.encode(params["F"], params["G"], x.astype(np.float64))
+    _, c = ap.mlp_forward(params["W1"], params["W2"], params["w3"], y, ap.bf16)
+    fmax = float(np.max(np.abs(params["F"])))
+    ok = ~np.any(near_bf16_midpoint(y, 2.5e-7 * fmax, 3e-5), axis=1)
+    scale = np.abs(c["yq"]) @ np.abs(np.asarray(params["W1"], dtype=np.float64)).T
+    ok &= ~np.any(near_bf16_midpoint(c["h1"], 4e-7 * scale, 3e-5), axis=1)
+    return x[ok]
 
 
 def make_model(shape, n_bricks, precision, max_points, seed, shrink=0.4):
