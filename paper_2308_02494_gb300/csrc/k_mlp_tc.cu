@@ -50,8 +50,25 @@ constexpr uint32_t kIdDY = tc::idesc_bf16(128, 128, false, true);   // dY (W1 re
 constexpr uint32_t kIdW = tc::idesc_bf16(128, 64, true, true);      // dW1^T, dW2^T
 
 __device__ __forceinline__ float bits(uint32_t u) { return __uint_as_float(u); }
+// bf16 pair {ReLU(lo), ReLU(hi)} (round to nearest even), one instruction.
+__device__ __forceinline__ uint32_t relu_pack(uint32_t lo, uint32_t hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(bits(hi)), "f"(bits(lo)));
+  return d;
+}
+// For a pair of non-negative bf16 values (ReLU outputs), 0xffff in each half that is
+// nonzero: adding 0x7fff to a half sets its bit 15 exactly when the half is nonzero
+// (never carrying into the other half), and the permute replicates bits 15 and 31
+// over their halves.
+__device__ __forceinline__ uint32_t nonzero_halves(uint32_t h) {
+  uint32_t m;
+  asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(m) : "r"(h + 0x7fff7fffu));
+  return m;
+}
 
-__global__ void __launch_bounds__(TNT, 2)
+// At most 200 registers: two CTAs (2 x 128 x 200) and one CTA of the density pass
+// beside them (256 x 56) fill the register file exactly.
+__global__ void __maxnreg__(200)
 k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ target) {
   extern __shared__ unsigned char raw[];
   __shared__ TileMap tm;
@@ -91,9 +108,9 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     tc::fence_after_sync();
   };
 
-  float dw3[64];
+  f2_t dw3p[32];   // dw3 partial sums of this thread's rows, as float pairs
 #pragma unroll
-  for (int j = 0; j < 64; ++j) dw3[j] = 0.f;
+  for (int j = 0; j < 32; ++j) dw3p[j] = 0ull;
   double sum_r2 = 0.0;
 
   // Weight gradients of brick b: tensor memory (dW1^T, dW2^T) and registers (dw3) to
@@ -124,15 +141,16 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < 64; ++j) {
-      float v = dw3[j];
+      float v = (j & 1) ? f2_hi(dw3p[j >> 1]) : f2_lo(dw3p[j >> 1]);
       v += __shfl_xor_sync(0xffffffffu, v, 16);
       v += __shfl_xor_sync(0xffffffffu, v, 8);
       v += __shfl_xor_sync(0xffffffffu, v, 4);
       v += __shfl_xor_sync(0xffffffffu, v, 2);
       v += __shfl_xor_sync(0xffffffffu, v, 1);
       if (lane == 0) atomicAdd(dw3s + j, v);
-      dw3[j] = 0.f;
     }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) dw3p[j] = 0ull;
     __syncthreads();
     if (tid < 64) atomicAdd(gr.dw3 + (int64_t)b * gr.sw3 + tid, dw3s[tid]);
     double s = sum_r2;
@@ -211,7 +229,7 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
       tc::ld16(trow + kColZ1 + c0, z);
       tc::ld_wait();
 #pragma unroll
-      for (int j = 0; j < 8; ++j) h[j] = pack_bf16(fmaxf(bits(z[2 * j]), 0.f), fmaxf(bits(z[2 * j + 1]), 0.f));
+      for (int j = 0; j < 8; ++j) h[j] = relu_pack(z[2 * j], z[2 * j + 1]);
       *reinterpret_cast<uint4*>(sm + TcLay::H1 + tc::sw128_off(r, c0, TT)) = make_uint4(h[0], h[1], h[2], h[3]);
       *reinterpret_cast<uint4*>(sm + TcLay::H1 + tc::sw128_off(r, c0 + 8, TT)) = make_uint4(h[4], h[5], h[6], h[7]);
     }
@@ -228,16 +246,22 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
       tc::commit(mbar);
     }
     wait_mma();
-    // ---- f, the loss, dm; dZ2 -> shared memory; dw3
-    float m = 0.f;
+    // ---- f, the loss, dm; dZ2 -> shared memory; dw3.  Z2 is read from tensor memory
+    //      once; the dot with w3, dw3 and dm w3 run on packed float pairs.
+    f2_t h2[32];
 #pragma unroll
     for (int c0 = 0; c0 < 64; c0 += 16) {
       uint32_t z[16];
       tc::ld16(trow + kColZ2 + c0, z);
       tc::ld_wait();
 #pragma unroll
-      for (int j = 0; j < 16; ++j) m = fmaf(fmaxf(bits(z[j]), 0.f), w3s[c0 + j], m);
+      for (int j = 0; j < 8; ++j) h2[c0 / 2 + j] = f2_pack(fmaxf(bits(z[2 * j]), 0.f), fmaxf(bits(z[2 * j + 1]), 0.f));
     }
+    const f2_t* w3p = reinterpret_cast<const f2_t*>(w3s);
+    f2_t macc = 0ull;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) macc = f2_fma(h2[j], w3p[j], macc);
+    const float m = f2_lo(macc) + f2_hi(macc);
     float dm;
     if (ws.upstream) {   // caller-supplied dL/df: dL/dm = dL/df (max - min)
       dm = rv ? vr * span : 0.f;
@@ -247,18 +271,17 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
       sum_r2 += (double)e * e;
       dm = 2.f * e * span * inv_n;
     }
+    const f2_t dm2 = f2_pack(dm, dm);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) dw3p[j] = f2_fma(dm2, h2[j], dw3p[j]);
 #pragma unroll
     for (int c0 = 0; c0 < 64; c0 += 16) {
-      uint32_t z[16], d[8];
-      tc::ld16(trow + kColZ2 + c0, z);
-      tc::ld_wait();
+      uint32_t d[8];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) dw3[c0 + j] = fmaf(dm, fmaxf(bits(z[j]), 0.f), dw3[c0 + j]);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float a = bits(z[2 * j]) > 0.f ? dm * w3s[c0 + 2 * j] : 0.f;
-        const float c = bits(z[2 * j + 1]) > 0.f ? dm * w3s[c0 + 2 * j + 1] : 0.f;
-        d[j] = pack_bf16(a, c);
+      for (int j = 0; j < 8; ++j) {   // ReLU outputs are never negative: > 0 iff nonzero
+        const f2_t q = f2_mul(dm2, w3p[c0 / 2 + j]);
+        const f2_t hh = h2[c0 / 2 + j];
+        d[j] = pack_bf16(f2_lo(hh) != 0.f ? f2_lo(q) : 0.f, f2_hi(hh) != 0.f ? f2_hi(q) : 0.f);
       }
       *reinterpret_cast<uint4*>(sm + TcLay::DZ2 + tc::sw128_off(r, c0, TT)) = make_uint4(d[0], d[1], d[2], d[3]);
       *reinterpret_cast<uint4*>(sm + TcLay::DZ2 + tc::sw128_off(r, c0 + 8, TT)) = make_uint4(d[4], d[5], d[6], d[7]);
@@ -292,7 +315,7 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
       const uint32_t hw[8] = {ha.x, ha.y, ha.z, ha.w, hb.x, hb.y, hb.z, hb.w};
 #pragma unroll
       for (int j = 0; j < 8; ++j)   // ReLU outputs are never negative: > 0 iff nonzero
-        d[j] = pack_bf16((hw[j] & 0x7fffu) ? bits(z[2 * j]) : 0.f, (hw[j] & 0x7fff0000u) ? bits(z[2 * j + 1]) : 0.f);
+        d[j] = pack_bf16(bits(z[2 * j]), bits(z[2 * j + 1])) & nonzero_halves(hw[j]);
       *reinterpret_cast<uint4*>(sm + TcLay::DZ1 + tc::sw128_off(r, c0, TT)) = make_uint4(d[0], d[1], d[2], d[3]);
       *reinterpret_cast<uint4*>(sm + TcLay::DZ1 + tc::sw128_off(r, c0 + 8, TT)) = make_uint4(d[4], d[5], d[6], d[7]);
     }

@@ -20,7 +20,7 @@
 //          Each box node then goes into the float32 gradient grid with one atomic.
 //          Points outside their tile's box (rounding at its faces; a batch that is not
 //          Morton-sorted) add their corners directly.
-#include "bf16_ops.cuh"
+#include "enc_ops.cuh"
 #include "kernels.h"
 #include <algorithm>
 #include <climits>
@@ -361,8 +361,6 @@ k_mlp(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ targ
 constexpr int ST = kMaxTilePoints;   // Morton-consecutive points per tile (at most)
 constexpr int SNT = 512;        // threads of k_scat (one CTA per SM)
 constexpr int SNW = SNT / 32;
-constexpr float kMagic = 12582912.f;        // 1.5 * 2^23: for |x| < 2^22, x + kMagic holds round(x)
-constexpr int32_t kMagicBits = 0x4B400000;  // in its low bits, offset by these bits of kMagic
 
 // Head of k_scat's dynamic shared memory; the tile's fixed-point node boxes follow it,
 // [group][node][channel][32 columns] int32 (see ScatMap).
@@ -584,31 +582,12 @@ __device__ uint2 tile_box(uint32_t code, const float* __restrict__ g, int R) {
     lo[d] = -1.f + unit * (float)uc[d];
     hi[d] = -1.f + unit * (float)(uc[d] + ext[d]);
   }
-  const float h = 0.5f * (float)(R - 1);
-  uint32_t blo = 0, bn = 0;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    float umin = __ldg(g + 4 * d + 3), umax = umin;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float a = __ldg(g + 4 * d + k);
-      const float p = a * lo[k], q = a * hi[k];
-      umin += fminf(p, q);
-      umax += fmaxf(p, q);
-    }
-    if (umax < -1.f || umin > 1.f) return make_uint2(0u, 0u);
-    const float s0 = fminf(fmaxf(fmaf(umin, h, h) - 1e-3f, 0.f), (float)(R - 1));
-    const float s1 = fminf(fmaxf(fmaf(umax, h, h) + 1e-3f, 0.f), (float)(R - 1));
-    const int c0 = min((int)s0, R - 2), c1 = min((int)s1, R - 2);
-    blo |= (uint32_t)c0 << (8 * d);
-    bn |= (uint32_t)(c1 - c0 + 2) << (8 * d);
-  }
-  return make_uint2(blo, bn);
+  return block_box(lo, hi, g, R);
 }
 
 // At most 96 registers: with them a CTA of the density pass (8 warps x 64) fits beside
 // the scatter's 16 warps in one SM's register file.
-template <int C>
+template <int C, bool EVEN_R>
 __global__ void __maxnreg__(96)
 k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -712,6 +691,8 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
       }
       const uint32_t oy = (uint32_t)nxb * kNodeBytes, oz = (uint32_t)(nxb * nyb) * kNodeBytes;
       const float hs = 0.5f * (float)(R - 1);
+      const float ct = hs - 0.5f + kMagic;   // an integer when R is even (axis_cell)
+      const int32_t mlox = kMagicBits + lox, mloy = kMagicBits + loy, mloz = kMagicBits + loz;
       // dL/dy of the next SU points is requested while the current SU are processed
       constexpr int SU = 4;
       uint32_t dn[SU];
@@ -738,24 +719,30 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
           // Eq. 2's set-up as make_cell computes it; for points inside the grid s lies in
           // [0, R-1] already (the rounding of fmaf is monotone), so no clamp is needed
           if (!((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f))) continue;
-          // (cell floor(s): it differs from min(floor(s), R-2) only at s = R-1, whose cell
-          // R-1 is never in a box and takes the exact path below)
-          Cell c;
-          const float sx = fmaf(ux, hs, hs), sy = fmaf(uy, hs, hs), sz = fmaf(uz, hs, hs);
-          c.cx = (int)sx; c.cy = (int)sy; c.cz = (int)sz;
-          c.wx = sx - (float)c.cx; c.wy = sy - (float)c.cy; c.wz = sz - (float)c.cz;
-          c.inside = true;
+          // (with R odd the cell is floor(s): it differs from min(floor(s), R-2) only at
+          // s = R-1, whose cell R-1 is never in a box and takes the exact path below)
+          float wx, wy, wz;
+          unsigned lx, ly, lz;   // cell relative to the box
+          if constexpr (EVEN_R) {
+            lx = (unsigned)(axis_cell(ux, hs, ct, wx) - mlox);
+            ly = (unsigned)(axis_cell(uy, hs, ct, wy) - mloy);
+            lz = (unsigned)(axis_cell(uz, hs, ct, wz) - mloz);
+          } else {
+            const float sx = fmaf(ux, hs, hs), sy = fmaf(uy, hs, hs), sz = fmaf(uz, hs, hs);
+            const int cx = (int)sx, cy = (int)sy, cz = (int)sz;
+            wx = sx - (float)cx; wy = sy - (float)cy; wz = sz - (float)cz;
+            lx = (unsigned)(cx - lox); ly = (unsigned)(cy - loy); lz = (unsigned)(cz - loz);
+          }
           const float g0 = __uint_as_float(d << 16), g1 = __uint_as_float(d & 0xffff0000u);
-          const unsigned lx = (unsigned)(c.cx - lox), ly = (unsigned)(c.cy - loy), lz = (unsigned)(c.cz - loz);
           if (boxed && lx < (unsigned)(nxb - 1) && ly < (unsigned)(nyb - 1) && lz < (unsigned)(nzb - 1)) {
-            const float ax = 1.f - c.wx, ay = 1.f - c.wy, az = 1.f - c.wz;
-            const float zy0 = az * ay, zy1 = az * c.wy, zy2 = c.wz * ay, zy3 = c.wz * c.wy;
+            const float ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
+            const float zy0 = az * ay, zy1 = az * wy, zy2 = wz * ay, zy3 = wz * wy;
             const float gs0 = g0 * scale, gs1 = g1 * scale;
             const uint32_t a0 = col_s + ((lz * (unsigned)nyb + ly) * (unsigned)nxb + lx) * kNodeBytes;
-            red_pair<C>(a0, zy0 * ax, zy0 * c.wx, gs0, gs1);
-            red_pair<C>(a0 + oy, zy1 * ax, zy1 * c.wx, gs0, gs1);
-            red_pair<C>(a0 + oz, zy2 * ax, zy2 * c.wx, gs0, gs1);
-            red_pair<C>(a0 + oy + oz, zy3 * ax, zy3 * c.wx, gs0, gs1);
+            red_pair<C>(a0, zy0 * ax, zy0 * wx, gs0, gs1);
+            red_pair<C>(a0 + oy, zy1 * ax, zy1 * wx, gs0, gs1);
+            red_pair<C>(a0 + oz, zy2 * ax, zy2 * wx, gs0, gs1);
+            red_pair<C>(a0 + oy + oz, zy3 * ax, zy3 * wx, gs0, gs1);
           } else {   // outside the tile's box (rounding at its faces, or an unsorted batch)
             scatter_point(dFi, make_cell(ux, uy, uz, R), R, C, g0, C == 2 ? g1 : 0.f);
           }
@@ -808,42 +795,7 @@ struct EncHead {
   float gs[kMaxGrids * 12];     // the brick's transforms
   ScatTile tile;
 };
-template <int C>
-using EncNode = std::conditional_t<C == 2, uint32_t, uint16_t>;   // one node: C bf16 values
-
-// Packed float pairs (two channels at once).
-__device__ __forceinline__ unsigned long long f2_bits(float lo, float hi) {
-  return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
-}
-__device__ __forceinline__ unsigned long long bf2_bits(uint32_t v) {   // bf16x2 -> f32x2
-  return f2_bits(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
-}
-// a + w (b - a) on both halves
-__device__ __forceinline__ unsigned long long lerp2(unsigned long long a, unsigned long long b,
-                                                    unsigned long long w) {
-  unsigned long long d, r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(b), "l"(a));
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(w), "l"(d), "l"(a));
-  return r;
-}
-
-// One staged node (C bf16 values) at shared address a + OFF.
-template <int C, int OFF>
-__device__ __forceinline__ uint32_t enc_node(uint32_t a) {
-  uint32_t v;
-  if constexpr (C == 2) asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
-  else asm volatile("ld.shared.u16 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
-  return v;
-}
-// Eq. 2 from the grid in global memory (a point outside its tile's box), packed as Y.
-template <int C>
-__device__ __noinline__ uint32_t enc_global(const __nv_bfloat16* Fi, Cell c, int R) {
-  float f0 = 0.f, f1 = 0.f;
-  trilinear_bf16_any(Fi, c, R, C, f0, f1);
-  return C == 2 ? pack_bf16(f0, f1) : (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f0));
-}
-
-template <int C>
+template <int C, bool EVEN_R>
 __global__ void __launch_bounds__(SNT, 2)
 k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn) {
   using E = EncNode<C>;
@@ -858,7 +810,6 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn)
   const int ntiles = ws.tile_ctr[0];
   const int64_t gsz = (int64_t)R * R * R * C;
   E* col = boxes + mp.grp * capn * 32 + lane;             // this thread's column
-  constexpr uint32_t kRow = 32 * sizeof(E);              // bytes of one node row
   const float hs = 0.5f * (float)(R - 1);
   // staging: M >= 32, the warps of a group split the nodes of their grids; M < 32, every
   // lane fills its own column and all warps split the nodes
@@ -883,92 +834,24 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn)
     }
     const int64_t p0 = T.start;
     const int np = T.count;
-    const int lvl = (int)((T.code >> 16) & 15u);
-    bool mine_in = true;
-    for (int p = tid; p < np; p += SNT) {
-      const float x = xyz[3 * (p0 + p)], y = xyz[3 * (p0 + p) + 1], z = xyz[3 * (p0 + p) + 2];
-      h.xs[p] = make_float4(x, y, z, 0.f);
-      mine_in &= (((morton_bin(x, y, z) >> 3) ^ (T.code & 0xffffu)) >> lvl) == 0u;
-    }
+    for (int p = tid; p < np; p += SNT)
+      h.xs[p] = make_float4(xyz[3 * (p0 + p)], xyz[3 * (p0 + p) + 1], xyz[3 * (p0 + p) + 2], 0.f);
     if (tid < M) h.box[tid] = tile_box(T.code, Gb + 12 * tid, R);
-    const bool in_block = __syncthreads_and(mine_in) != 0;
-    const uint2 bx = h.box[mp.g];
-    const int nxb = (int)(bx.y & 0xffu), nyb = (int)((bx.y >> 8) & 0xffu), nzb = (int)((bx.y >> 16) & 0xffu);
-    const int lox = (int)(bx.x & 0xffu), loy = (int)((bx.x >> 8) & 0xffu), loz = (int)((bx.x >> 16) & 0xffu);
-    const int nodes = nxb * nyb * nzb;
-    const bool boxed = nodes > 0 && nodes <= capn;
+    __syncthreads();
+    const EncBox eb = enc_box<C>(h.box[mp.g], capn, su32(col));
     const E* Fg = reinterpret_cast<const E*>(md.F16 + (int64_t)b * md.sF + mp.g * gsz);
-    if (boxed) {   // stage the grid's box, four node loads in flight
-      int qz = n0 / (nxb * nyb), qr = n0 - qz * nxb * nyb;
-      int qy = qr / nxb, qx = qr - qy * nxb;
-      for (int n = n0; n < nodes; n += 4 * nstep) {
-        E v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          v[u] = 0;
-          if (n + u * nstep < nodes) v[u] = __ldg(Fg + ((int64_t)(loz + qz) * R + (loy + qy)) * R + lox + qx);
-          qx += nstep;
-          while (qx >= nxb) {
-            qx -= nxb;
-            if (++qy == nyb) { qy = 0; ++qz; }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (n + u * nstep < nodes) col[(n + u * nstep) * 32] = v[u];
-      }
-    }
+    if (eb.boxed) enc_stage<C>(eb, Fg, R, col, n0, nstep);
     float gi[12];
 #pragma unroll
     for (int j = 0; j < 12; ++j) gi[j] = h.gs[12 * mp.g + j];
     __syncthreads();
-    const uint32_t col_s = su32(col);
-    const uint32_t oy = (uint32_t)nxb * kRow, oz = (uint32_t)(nxb * nyb) * kRow;   // bytes
+    const float ct = hs - 0.5f + kMagic;   // an integer when R is even (axis_cell)
     E* Yt = reinterpret_cast<E*>(ws.Y) + p0 * M + mp.g;
     const __nv_bfloat16* Fi = md.F16 + (int64_t)b * md.sF + mp.g * gsz;
 #pragma unroll 2
     for (int p = mp.pg; p < np; p += mp.npg) {
       const float4 x = h.xs[p];
-      float ux, uy, uz;
-      affine(gi, x.x, x.y, x.z, ux, uy, uz);
-      uint32_t yv = 0u;
-      if ((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f)) {
-        // Eq. 2's set-up as make_cell computes it: inside the grid s lies in [0, R-1] (the
-        // rounding of fmaf is monotone); the cell min(floor(s), R-2) differs from floor(s)
-        // only at s = R-1, whose cell R-1 is never in a box and takes the exact path below
-        Cell c;
-        const float sx = fmaf(ux, hs, hs), sy = fmaf(uy, hs, hs), sz = fmaf(uz, hs, hs);
-        c.cx = (int)sx; c.cy = (int)sy; c.cz = (int)sz;
-        c.wx = sx - (float)c.cx; c.wy = sy - (float)c.cy; c.wz = sz - (float)c.cz;
-        c.inside = true;
-        const unsigned lx = (unsigned)(c.cx - lox), ly = (unsigned)(c.cy - loy), lz = (unsigned)(c.cz - loz);
-        if (boxed && lx < (unsigned)(nxb - 1) && ly < (unsigned)(nyb - 1) && lz < (unsigned)(nzb - 1)) {
-          const uint32_t a0 = col_s + ((lz * (unsigned)nyb + ly) * (unsigned)nxb + lx) * kRow;
-          const uint32_t a1 = a0 + oy, a2 = a0 + oz, a3 = a2 + oy;
-          if constexpr (C == 2) {
-            const unsigned long long wx = f2_bits(c.wx, c.wx), wy = f2_bits(c.wy, c.wy), wz = f2_bits(c.wz, c.wz);
-            const unsigned long long e0 = lerp2(bf2_bits(enc_node<C, 0>(a0)), bf2_bits(enc_node<C, kRow>(a0)), wx);
-            const unsigned long long e1 = lerp2(bf2_bits(enc_node<C, 0>(a1)), bf2_bits(enc_node<C, kRow>(a1)), wx);
-            const unsigned long long e2 = lerp2(bf2_bits(enc_node<C, 0>(a2)), bf2_bits(enc_node<C, kRow>(a2)), wx);
-            const unsigned long long e3 = lerp2(bf2_bits(enc_node<C, 0>(a3)), bf2_bits(enc_node<C, kRow>(a3)), wx);
-            const unsigned long long f = lerp2(lerp2(e0, e1, wy), lerp2(e2, e3, wy), wz);
-            yv = pack_bf16(__uint_as_float((uint32_t)f), __uint_as_float((uint32_t)(f >> 32)));
-          } else {
-            auto v = [](uint32_t q) { return __uint_as_float(q << 16); };
-            const float v0 = v(enc_node<C, 0>(a0)), v1 = v(enc_node<C, kRow>(a0));
-            const float v2 = v(enc_node<C, 0>(a1)), v3 = v(enc_node<C, kRow>(a1));
-            const float v4 = v(enc_node<C, 0>(a2)), v5 = v(enc_node<C, kRow>(a2));
-            const float v6 = v(enc_node<C, 0>(a3)), v7 = v(enc_node<C, kRow>(a3));
-            const float e0 = fmaf(c.wx, v1 - v0, v0), e1 = fmaf(c.wx, v3 - v2, v2);
-            const float e2 = fmaf(c.wx, v5 - v4, v4), e3 = fmaf(c.wx, v7 - v6, v6);
-            const float f01 = fmaf(c.wy, e1 - e0, e0), f23 = fmaf(c.wy, e3 - e2, e2);
-            yv = __bfloat16_as_ushort(__float2bfloat16_rn(fmaf(c.wz, f23 - f01, f01)));
-          }
-        } else {   // outside the tile's box: the corners from global memory
-          yv = enc_global<C>(Fi, make_cell(ux, uy, uz, R), R);
-        }
-      }
-      Yt[p * M] = (E)yv;
+      Yt[p * M] = (E)encode_point<C, EVEN_R>(gi, x.x, x.y, x.z, eb, hs, ct, R, Fi);
     }
   }
 }
@@ -1093,7 +976,7 @@ int scat_capn(int M, int C) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, (const void*)k_scat<2>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
+  if (cudaFuncGetAttributes(&fa, (const void*)k_scat<2, true>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
   const int ngrp = M >= 32 ? M / 32 : 1;
   // leave room for one CTA of the density pass that may run beside the scatter
   const long long block = std::min<long long>(optin, (long long)per_sm - 1024 - kDensityCtaSmem);
@@ -1111,7 +994,7 @@ int enc_capn(int M, int C) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, (const void*)k_enc<2>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
+  if (cudaFuncGetAttributes(&fa, (const void*)k_enc<2, true>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
   const int ngrp = M >= 32 ? M / 32 : 1;
   const long long room = (long long)per_sm / 2 - 1024 - stat - (long long)sizeof(EncHead);
   return room > 0 ? (int)(room / ((long long)ngrp * 32 * (C == 2 ? 4 : 2))) : 0;
@@ -1149,7 +1032,9 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
   {
     const int capn = enc_capn(md.M, md.C);
     const size_t smem = enc_smem(md.M, md.C, capn);
-    const void* kern = md.C == 2 ? (const void*)k_enc<2> : (const void*)k_enc<1>;
+    const bool even = (md.R & 1) == 0;
+    const void* kern = md.C == 2 ? (even ? (const void*)k_enc<2, true> : (const void*)k_enc<2, false>)
+                                 : (even ? (const void*)k_enc<1, true> : (const void*)k_enc<1, false>);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
     const int grid = L.num_sms * occupancy(kern, SNT, smem);
@@ -1196,14 +1081,15 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
     const int capn = scat_capn(md.M, md.C);
     if (capn < 8) return cudaErrorInvalidConfiguration;
     const size_t smem = scat_smem(md.M, md.C, capn);
-    const void* kern = md.C == 2 ? (const void*)k_scat<2> : (const void*)k_scat<1>;
+    const bool even = (md.R & 1) == 0;
+    const void* kern = md.C == 2 ? (even ? (const void*)k_scat<2, true> : (const void*)k_scat<2, false>)
+                                 : (even ? (const void*)k_scat<1, true> : (const void*)k_scat<1, false>);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
     const int grid = L.num_sms * occupancy(kern, SNT, smem);
     mark_start(2);
-    if (md.C == 2) k_scat<2><<<grid, SNT, smem, L.stream>>>(md, gr, br, ws, xyz, capn);
-    else k_scat<1><<<grid, SNT, smem, L.stream>>>(md, gr, br, ws, xyz, capn);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    void* args[] = {(void*)&md, (void*)&gr, (void*)&br, (void*)&ws, (void*)&xyz, (void*)&capn};
+    if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(SNT), args, smem, L.stream)) != cudaSuccess) return e;
     mark_stop(2);
   }
   if (ws.rec_dg) {
