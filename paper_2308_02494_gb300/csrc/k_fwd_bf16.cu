@@ -25,7 +25,7 @@ struct FwdLay {
 };
 
 template <int K>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT, 3)
 k_fwd_bf16(Model md, Bricks brp, const float* __restrict__ xyz, float* __restrict__ out) {
   using L = FwdLay<K>;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -168,7 +168,7 @@ cudaError_t launch_k(const Launch& L, const Model& md, const Bricks& br, const f
   auto kern = k_fwd_bf16<K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  int grid = 2 * L.num_sms;
+  int grid = 3 * L.num_sms;
   if (!br.dev) {
     int total = 0;
     for (int b = 0; b < br.n; ++b) total += (int)((br.off[b + 1] - br.off[b] + T - 1) / T);

@@ -96,15 +96,21 @@ __global__ void __launch_bounds__(256) k_render_gen(RenderParams rp, int pix0, i
                                                     uint32_t* __restrict__ cnt) {
   __shared__ uint32_t s_cnt[SRN_MAX_BRICKS], s_base[SRN_MAX_BRICKS];
   const int nb = rp.grid[0] * rp.grid[1] * rp.grid[2];
-  const int64_t total = (int64_t)npix * rp.samples;
+  const int64_t total = render_slots(rp.rg, rp.jb, rp.samples, npix);
+  const int nsb = (rp.samples + rp.jb - 1) / rp.jb;
   const int lane = threadIdx.x & 31;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
     for (int k = threadIdx.x; k < nb; k += blockDim.x) s_cnt[k] = 0;
     __syncthreads();
     const int64_t idx = base + threadIdx.x;
     uint32_t b = 0xffffffffu;
-    if (idx < total) {
-      const int ray = (int)(idx / rp.samples), j = (int)(idx % rp.samples);
+    // the slot's ray and sample (the inverse of render_slot)
+    const int js = (int)(idx % rp.jb);
+    const int64_t q1 = idx / rp.jb;
+    const int rl = (int)(q1 % rp.rg);
+    const int64_t q2 = q1 / rp.rg;
+    const int ray = (int)(q2 / nsb) * rp.rg + rl, j = (int)(q2 % nsb) * rp.jb + js;
+    if (idx < total && ray < npix && j < rp.samples) {
       const Ray r = make_ray(rp, pixel_of(rp, pix0 + ray));
       if (r.hit) {
         const float t = r.t0 + ((float)j + 0.5f) * r.dt;
@@ -203,7 +209,7 @@ __global__ void k_render_composite(RenderParams rp, int pix0, int npix, const ui
     const float k = r.dt / (2.f / 512.f);
     const float inv_span = 1.f / (rp.vmax - rp.vmin);
     for (int j = 0; j < rp.samples; ++j) {
-      const float f = val[pos[(int64_t)ray * rp.samples + j]];
+      const float f = val[pos[render_slot(rp.rg, rp.jb, rp.samples, ray, j)]];
       const float s = fminf(fmaxf((f - rp.vmin) * inv_span, 0.f), 1.f) * 255.f;
       const int i0 = min((int)s, 254);
       const float fr = s - (float)i0;
@@ -261,7 +267,7 @@ int blocks_for(int64_t n, int threads, int num_sms) {
 
 cudaError_t launch_render_batch(const Launch& L, const RenderParams& rp, const RenderWs& w, int pix0,
                                 int npix, const Model& md, const float* lut, float* rgba) {
-  const int64_t total = (int64_t)npix * rp.samples;
+  const int64_t total = render_slots(rp.rg, rp.jb, rp.samples, npix);
   const int nb = rp.grid[0] * rp.grid[1] * rp.grid[2];
   cudaError_t e = cudaMemsetAsync(w.cnt, 0, sizeof(uint32_t) * nb, L.stream);
   if (e != cudaSuccess) return e;

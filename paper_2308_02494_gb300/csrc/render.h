@@ -10,12 +10,26 @@ struct RenderParams {
   int32_t width, height, samples;
   int32_t order;    // 0: raster order; 1: the progressive (image-hierarchy) order
   int32_t levels;   // L: the coarsest hierarchy level, 2^L >= max(width, height)
+  // Sample slots of a batch: groups of rg consecutive rays x blocks of jb consecutive
+  // samples (render_slot), so that 128 consecutive slots (rg = 8, jb = 16) are a compact
+  // bundle of ray segments: the forward query's tiles then read few cache lines per grid.
+  int32_t rg, jb;
   int32_t grid[3];
   int64_t vox;
   float vmin, vmax;
   int32_t lo[SRN_MAX_BRICKS][3];
   int32_t hi[SRN_MAX_BRICKS][3];
 };
+
+// Slot of sample j of ray `ray` in a batch, and the number of slots of npix rays (padded
+// to whole ray groups and sample blocks; padding slots hold no sample).
+__host__ __device__ inline int64_t render_slot(int rg, int jb, int samples, int ray, int j) {
+  const int nsb = (samples + jb - 1) / jb;
+  return (((int64_t)(ray / rg) * nsb + j / jb) * rg + ray % rg) * jb + j % jb;
+}
+__host__ __device__ inline int64_t render_slots(int rg, int jb, int samples, int npix) {
+  return (int64_t)((npix + rg - 1) / rg) * rg * ((samples + jb - 1) / jb) * jb;
+}
 
 struct RenderWs {
   float* loc;       // [max_points][3] brick-local sample coordinates, ray order

@@ -948,6 +948,10 @@ srn_status render_params(srn_handle* h, const srn_camera* cam, const float* lut,
   rp.width = width; rp.height = height; rp.samples = samples;
   rp.order = 0;
   rp.levels = 0;
+  // bundles of 8 rays x 16 samples when a batch holds at least one bundle of whole rays
+  const bool bundle = 8 * (((int64_t)samples + 15) / 16 * 16) <= h->max_points;
+  rp.rg = bundle ? 8 : 1;
+  rp.jb = bundle ? 16 : 1;
   while ((1 << rp.levels) < std::max(width, height)) ++rp.levels;
   for (int a = 0; a < 3; ++a) rp.grid[a] = grid[a];
   rp.vox = vox; rp.vmin = vmin; rp.vmax = vmax;
@@ -974,7 +978,9 @@ srn_status render_pixels(srn_handle* h, void* stream, const srn::RenderParams& r
   w.val = reinterpret_cast<float*>(ws + h->wl.r_val);
   w.cnt = reinterpret_cast<uint32_t*>(ws + h->wl.r_cnt);
   w.off = reinterpret_cast<int64_t*>(ws + h->wl.r_off);
-  const int64_t batch = h->max_points / rp.samples;
+  // whole ray groups whose slots fit the workspace's max_points samples
+  const int64_t spr = ((int64_t)rp.samples + rp.jb - 1) / rp.jb * rp.jb;
+  const int64_t batch = h->max_points / spr / rp.rg * rp.rg;
   const srn::Model md = h->model();
   for (int64_t p0 = first; p0 < first + count; p0 += batch) {
     const int n = (int)std::min<int64_t>(batch, first + count - p0);
