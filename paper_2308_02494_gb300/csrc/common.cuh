@@ -67,6 +67,10 @@ struct TrainWs {
   int32_t upstream; // 1: the target slot holds dL/df (no L_rec); 0: MSE against targets
   __nv_bfloat16* Y;   // [N][K] features (BF16 training pass)
   __nv_bfloat16* dY;  // [N][M][C] dL/dy, point-major like Y (BF16 training pass)
+  // [decoder tiles][M] the bf16 bits of the largest |dL/dy| of each grid over each
+  // 128-point decoder tile (tiles numbered as build_tile_map numbers them for 128), or
+  // NULL when the decoder does not produce them (the scatter then finds its scales itself)
+  uint16_t* gmax_blk;
   int32_t* ustart;    // [B][kUnits + 1] first point of each Morton unit (BF16 scatter tiles)
   const uint32_t* bin_start;   // [B][kSortBins] the sampler's bin starts of this batch, or NULL
   struct ScatTile* tiles;  // scatter tiles (BF16 training pass)

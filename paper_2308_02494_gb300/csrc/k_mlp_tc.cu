@@ -41,6 +41,11 @@ struct TcLay {
   static constexpr uint32_t DW3 = W3 + 256;  // [64] f32 reduction scratch
   static constexpr uint32_t BYTES = DW3 + 256;
 };
+// Staging of dL/dy for its coalesced store: 16 chunk columns of 128 rows x 16 bytes,
+// padded by 16 bytes so both the row-wise writes and the chunk-wise reads are
+// conflict-free; it spans H1, DZ2 and part of DZ1, all free by then.
+constexpr uint32_t kDyStage = TcLay::H1, kDyChunkStride = 128 * 16 + 16;
+static_assert(kDyStage + 16 * kDyChunkStride <= TcLay::W3, "dL/dy staging overlaps w3");
 // Tensor-memory columns.
 constexpr uint32_t kColZ1 = 0, kColZ2 = 64, kColDY = 0, kColDW1 = 128, kColDW2 = 192, kCols = 256;
 
@@ -74,6 +79,7 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
   __shared__ TileMap tm;
   __shared__ Bricks br;
   __shared__ uint32_t tslot;
+  __shared__ uint32_t s_gmax[TK];   // largest |dL/dy| bits per grid of the tile being written
   __shared__ __align__(8) unsigned long long mbar_s;
   load_bricks(brp, br);
   const uint32_t base0 = su32(raw), base = (base0 + 1023u) & ~1023u;
@@ -90,6 +96,7 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tc::tmem_alloc(su32(&tslot), kCols);
+  if (tid < TK) s_gmax[tid] = 0u;
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -224,14 +231,17 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     wait_mma();
     // ---- H1 = ReLU(Z1) -> shared memory
 #pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-      uint32_t z[16], h[8];
-      tc::ld16(trow + kColZ1 + c0, z);
+    for (int c0 = 0; c0 < 64; c0 += 32) {   // two tensor-memory loads per wait
+      uint32_t z[32], h[16];
+      tc::ld16(trow + kColZ1 + c0, *reinterpret_cast<uint32_t(*)[16]>(z));
+      tc::ld16(trow + kColZ1 + c0 + 16, *reinterpret_cast<uint32_t(*)[16]>(z + 16));
       tc::ld_wait();
 #pragma unroll
-      for (int j = 0; j < 8; ++j) h[j] = relu_pack(z[2 * j], z[2 * j + 1]);
-      *reinterpret_cast<uint4*>(sm + TcLay::H1 + tc::sw128_off(r, c0, TT)) = make_uint4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<uint4*>(sm + TcLay::H1 + tc::sw128_off(r, c0 + 8, TT)) = make_uint4(h[4], h[5], h[6], h[7]);
+      for (int j = 0; j < 16; ++j) h[j] = relu_pack(z[2 * j], z[2 * j + 1]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(sm + TcLay::H1 + tc::sw128_off(r, c0 + 8 * q, TT)) =
+            make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -250,12 +260,13 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     //      once; the dot with w3, dw3 and dm w3 run on packed float pairs.
     f2_t h2[32];
 #pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-      uint32_t z[16];
-      tc::ld16(trow + kColZ2 + c0, z);
+    for (int c0 = 0; c0 < 64; c0 += 32) {   // two tensor-memory loads per wait
+      uint32_t z[32];
+      tc::ld16(trow + kColZ2 + c0, *reinterpret_cast<uint32_t(*)[16]>(z));
+      tc::ld16(trow + kColZ2 + c0 + 16, *reinterpret_cast<uint32_t(*)[16]>(z + 16));
       tc::ld_wait();
 #pragma unroll
-      for (int j = 0; j < 8; ++j) h2[c0 / 2 + j] = f2_pack(fmaxf(bits(z[2 * j]), 0.f), fmaxf(bits(z[2 * j + 1]), 0.f));
+      for (int j = 0; j < 16; ++j) h2[c0 / 2 + j] = f2_pack(fmaxf(bits(z[2 * j]), 0.f), fmaxf(bits(z[2 * j + 1]), 0.f));
     }
     const f2_t* w3p = reinterpret_cast<const f2_t*>(w3s);
     f2_t macc = 0ull;
@@ -338,18 +349,62 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     wait_mma();
     if (tile + 1 < te && !gave_up) prefetch(tile + 1);   // Y has been read by every MMA of this tile
     // ---- dL/dy to global memory, point-major bf16: row p0 + r holds the K features'
-    //      gradients in feature order (grid-major, channel-minor, as Y)
-#pragma unroll
-    for (int c0 = 0; c0 < TK; c0 += 16) {
-      uint32_t z[16], d[8];
-      tc::ld16(trow + kColDY + c0, z);
+    //      gradients in feature order (grid-major, channel-minor, as Y).  Staged in the
+    //      (now free) H1 / dZ buffers as 16 column chunks of 16 bytes, chunk k of row r at
+    //      k * kDyChunkStride + 16 r (conflict-free both ways), then copied out with
+    //      coalesced stores: a warp writes two whole rows (512 contiguous bytes).  One
+    //      thread's row written with its own 16-byte stores would touch 32 scattered
+    //      sectors per warp instruction.
+#pragma unroll 1
+    for (int c0 = 0; c0 < TK; c0 += 32) {
+      uint32_t za[16], zb[16], d[16];
+      tc::ld16(trow + kColDY + c0, za);
+      tc::ld16(trow + kColDY + c0 + 16, zb);
       tc::ld_wait();
 #pragma unroll
-      for (int i = 0; i < 8; ++i) d[i] = pack_bf16(bits(z[2 * i]), bits(z[2 * i + 1]));
-      if (rv) {
-        uint4* o = reinterpret_cast<uint4*>(ws.dY + (p0 + r) * TK + c0);
-        o[0] = make_uint4(d[0], d[1], d[2], d[3]);
-        o[1] = make_uint4(d[4], d[5], d[6], d[7]);
+      for (int i = 0; i < 8; ++i) {
+        d[i] = pack_bf16(bits(za[2 * i]), bits(za[2 * i + 1]));
+        d[8 + i] = pack_bf16(bits(zb[2 * i]), bits(zb[2 * i + 1]));
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(sm + kDyStage + (c0 / 8 + q) * kDyChunkStride + 16 * r) =
+            make_uint4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+    }
+    __syncthreads();
+    {  // copy-out; thread t always handles chunk t mod 16, so it also takes the largest
+       // |dL/dy| of that chunk's features over the tile (for the scatter's fixed-point
+       // scales), reduced over the threads of the same chunk
+      uint32_t mx[4] = {0u, 0u, 0u, 0u};
+      for (int q = tid; q < np * (TK / 8); q += TNT) {
+        const int row = q >> 4, k = q & 15;
+        const uint4 v = *reinterpret_cast<const uint4*>(sm + kDyStage + k * kDyChunkStride + 16 * row);
+        *reinterpret_cast<uint4*>(ws.dY + (p0 + row) * TK + 8 * k) = v;
+        mx[0] = __vmaxu2(mx[0], v.x & 0x7fff7fffu);
+        mx[1] = __vmaxu2(mx[1], v.y & 0x7fff7fffu);
+        mx[2] = __vmaxu2(mx[2], v.z & 0x7fff7fffu);
+        mx[3] = __vmaxu2(mx[3], v.w & 0x7fff7fffu);
+      }
+      if (ws.gmax_blk) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mx[j] = __vmaxu2(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], 16));
+        if (lane < 16) {
+          const int k = tid & 15;   // features 8k .. 8k + 7
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (md.C == 2) {
+              atomicMax(s_gmax + 4 * k + j, max(mx[j] & 0xffffu, mx[j] >> 16));
+            } else {
+              atomicMax(s_gmax + 8 * k + 2 * j, mx[j] & 0xffffu);
+              atomicMax(s_gmax + 8 * k + 2 * j + 1, mx[j] >> 16);
+            }
+          }
+        }
+        __syncthreads();
+        if (tid < md.M) {
+          ws.gmax_blk[(int64_t)tile * md.M + tid] = (uint16_t)s_gmax[tid];
+          s_gmax[tid] = 0u;
+        }
       }
     }
     fresh = false;

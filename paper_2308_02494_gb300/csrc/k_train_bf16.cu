@@ -594,7 +594,9 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
   ScatHead& h = *reinterpret_cast<ScatHead*>(smraw);
   int32_t* acc = reinterpret_cast<int32_t*>(smraw + sizeof(ScatHead));
   __shared__ Bricks br;
+  __shared__ TileMap dtm;   // the decoder's 128-point tiles (ws.gmax_blk)
   load_bricks(brp, br);
+  if (threadIdx.x == 0) build_tile_map(br, 128, dtm);
   const int tid = threadIdx.x, lane = tid & 31;
   const int M = md.M, R = md.R;
   const ScatMap mp = scat_map(M);
@@ -650,13 +652,19 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
     }
     if (tid < M) {
       h.box[tid] = tile_box(T.code, Gb + 12 * tid, R);
-      h.gmax[tid] = 0u;
+      uint32_t mb = 0u;
+      if (ws.gmax_blk) {   // the decoder's maxima of the 128-point tiles overlapping this tile
+        const int64_t lp = p0 - br.off[b];
+        const int d0 = dtm.first[b] + (int)(lp / 128), d1 = dtm.first[b] + (int)((lp + np - 1) / 128);
+        for (int d = d0; d <= d1; ++d) mb = max(mb, (uint32_t)ws.gmax_blk[(int64_t)d * M + tid]);
+      }
+      h.gmax[tid] = mb;
     }
     // the block's boxes bound the points only if all of them lie in the block (always,
     // for a Morton-sorted batch); otherwise points outside a box add their corners directly
     const bool in_block = __syncthreads_and(mine_in) != 0;
-    {  // largest |dL/dy| of every grid over the tile (eight loads in flight; the rows were
-       // prefetched into L2 while the previous tile ran)
+    if (!ws.gmax_blk) {  // largest |dL/dy| of every grid over the tile (eight loads in flight; the
+                         // rows were prefetched into L2 while the previous tile ran)
       uint32_t mx = 0u;
       for (int p = mp.pg; p < np; p += 8 * mp.npg) {
         uint32_t d[8];

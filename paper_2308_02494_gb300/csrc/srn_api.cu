@@ -81,7 +81,7 @@ void make_layout(const srn_config* c, srn_layout* L) {
 
 // Workspace carving (every piece 256-byte aligned).
 struct WsLayout {
-  size_t state, acc, gsum, rsum, rho, herr, sort_tmp, sort_rank, sort_hist, feat, dfeat, ustart, tiles, tile_ctr;
+  size_t state, acc, gsum, rsum, rho, herr, sort_tmp, sort_rank, sort_hist, feat, dfeat, gmax, ustart, tiles, tile_ctr;
   size_t sched, sring;
   size_t r_loc, r_rank, r_bid, r_pos, r_xyz, r_val, r_cnt, r_off, total;
 };
@@ -102,6 +102,9 @@ WsLayout ws_layout(const srn_config* c, int64_t maxp) {
   const size_t kbytes = c->precision == SRN_BF16 ? sizeof(uint16_t) * c->n_grids * c->channels : 0;
   w.feat = o; o += align256(kbytes * maxp);
   w.dfeat = o; o += align256(kbytes * maxp);
+  // largest |dL/dy| per grid and 128-point decoder tile (tcgen05 decoder, K = 128)
+  const int64_t dec_tiles = maxp / 128 + c->n_bricks + 1;
+  w.gmax = o; o += c->precision == SRN_BF16 ? align256(sizeof(uint16_t) * srn::kMaxGrids * dec_tiles) : 0;
   // BF16 tiles: unit starts, and at most one tile per unit plus one per kMinTilePoints
   // points (the smallest tile any tuning allows)
   const bool bf16 = c->precision == SRN_BF16;
@@ -196,6 +199,8 @@ struct srn_handle {
     w.upstream = 0;
     w.Y = reinterpret_cast<__nv_bfloat16*>(ws + wl.feat);
     w.dY = reinterpret_cast<__nv_bfloat16*>(ws + wl.dfeat);
+    w.gmax_blk = cfg.precision == SRN_BF16 && cfg.n_grids * cfg.channels == 128
+                     ? reinterpret_cast<uint16_t*>(ws + wl.gmax) : nullptr;
     w.ustart = reinterpret_cast<int32_t*>(ws + wl.ustart);
     w.tiles = reinterpret_cast<srn::ScatTile*>(ws + wl.tiles);
     w.tile_ctr = reinterpret_cast<int32_t*>(ws + wl.tile_ctr);
