@@ -45,6 +45,18 @@ __device__ __forceinline__ unsigned long long lerp2(unsigned long long a, unsign
   return r;
 }
 
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 // One staged node (C bf16 values) at shared address a + OFF.
 template <int C, int OFF>
 __device__ __forceinline__ uint32_t enc_node(uint32_t a) {

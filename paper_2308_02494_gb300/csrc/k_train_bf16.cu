@@ -427,6 +427,43 @@ __device__ __forceinline__ void red_pair(uint32_t a, float wa, float wb, float g
   }
 }
 
+// The 8 corners x C channels of one (point, grid) whose cell lies in the box: corner
+// (i, j, k) of the cell at a0 (+ i node, + j oy, + k oz) gets round(Wx_i Wy_j Wz_k g scale)
+// for each channel g of dL/dy (bf16 bits d), the products formed channel pairs at a time
+// as ((g scale) Wz_k) Wy_j, and the Wx_i factor fused into the rounding FMA.
+template <int C>
+__device__ __forceinline__ void red_cell(uint32_t a0, uint32_t oy, uint32_t oz, float wx, float wy, float wz,
+                                         uint32_t d, float scale) {
+  if constexpr (C == 2) {
+    const unsigned long long one = f2_bits(1.f, 1.f), mm = f2_bits(kMagic, kMagic);
+    const unsigned long long wx2 = f2_bits(wx, wx), wy2 = f2_bits(wy, wy), wz2 = f2_bits(wz, wz);
+    unsigned long long ax2, ay2, az2;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ax2) : "l"(one), "l"(wx2));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ay2) : "l"(one), "l"(wy2));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(az2) : "l"(one), "l"(wz2));
+    const unsigned long long gs = mul2(bf2_bits(d), f2_bits(scale, scale));
+    const unsigned long long z0 = mul2(az2, gs), z1 = mul2(wz2, gs);
+    const unsigned long long yz[4] = {mul2(ay2, z0), mul2(wy2, z0), mul2(ay2, z1), mul2(wy2, z1)};
+    const uint32_t a[4] = {a0, a0 + oy, a0 + oz, a0 + oy + oz};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned long long va = fma2(ax2, yz[j], mm), vb = fma2(wx2, yz[j], mm);
+      red_s32<0>(a[j], (int32_t)(uint32_t)va - kMagicBits);
+      red_s32<128>(a[j], (int32_t)(uint32_t)(va >> 32) - kMagicBits);
+      red_s32<256>(a[j], (int32_t)(uint32_t)vb - kMagicBits);
+      red_s32<384>(a[j], (int32_t)(uint32_t)(vb >> 32) - kMagicBits);
+    }
+  } else {
+    const float ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
+    const float zy0 = az * ay, zy1 = az * wy, zy2 = wz * ay, zy3 = wz * wy;
+    const float gs0 = __uint_as_float(d << 16) * scale;
+    red_pair<C>(a0, zy0 * ax, zy0 * wx, gs0, 0.f);
+    red_pair<C>(a0 + oy, zy1 * ax, zy1 * wx, gs0, 0.f);
+    red_pair<C>(a0 + oz, zy2 * ax, zy2 * wx, gs0, 0.f);
+    red_pair<C>(a0 + oy + oz, zy3 * ax, zy3 * wx, gs0, 0.f);
+  }
+}
+
 // dL/dy of point p (global index) for grid g: C bf16 values in the low bits.
 template <int C>
 __device__ __forceinline__ uint32_t dy_bits(const __nv_bfloat16* dY, int64_t p, int M, int g) {
@@ -717,42 +754,48 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
 #pragma unroll
         for (int u = 0; u < SU; ++u) dc[u] = dn[u];
         load_next(p + SU * mp.npg);
+        // the cells and weights of all SU points first, without branches, so that their
+        // dependency chains overlap; then the reductions point by point
+        uint32_t ad[SU];            // box address of the cell's first corner; ~0u: not in the box
+        float wxs[SU], wys[SU], wzs[SU];
+        uint32_t live = 0u;         // bit u: nonzero dL/dy and inside the grid
 #pragma unroll
         for (int u = 0; u < SU; ++u) {
-          const uint32_t d = dc[u];
-          if (!(d & kNz)) continue;   // zero dL/dy, or past the tile's last point
-          const float4 x = h.xs[p + u * mp.npg];
+          const int q = p + u * mp.npg;
+          const float4 x = h.xs[q < np ? q : p];
           float ux, uy, uz;
           affine(gi, x.x, x.y, x.z, ux, uy, uz);
           // Eq. 2's set-up as make_cell computes it; for points inside the grid s lies in
           // [0, R-1] already (the rounding of fmaf is monotone), so no clamp is needed
-          if (!((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f))) continue;
           // (with R odd the cell is floor(s): it differs from min(floor(s), R-2) only at
           // s = R-1, whose cell R-1 is never in a box and takes the exact path below)
-          float wx, wy, wz;
+          const bool in = (dc[u] & kNz) && (fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f);
           unsigned lx, ly, lz;   // cell relative to the box
           if constexpr (EVEN_R) {
-            lx = (unsigned)(axis_cell(ux, hs, ct, wx) - mlox);
-            ly = (unsigned)(axis_cell(uy, hs, ct, wy) - mloy);
-            lz = (unsigned)(axis_cell(uz, hs, ct, wz) - mloz);
+            lx = (unsigned)(axis_cell(ux, hs, ct, wxs[u]) - mlox);
+            ly = (unsigned)(axis_cell(uy, hs, ct, wys[u]) - mloy);
+            lz = (unsigned)(axis_cell(uz, hs, ct, wzs[u]) - mloz);
           } else {
             const float sx = fmaf(ux, hs, hs), sy = fmaf(uy, hs, hs), sz = fmaf(uz, hs, hs);
             const int cx = (int)sx, cy = (int)sy, cz = (int)sz;
-            wx = sx - (float)cx; wy = sy - (float)cy; wz = sz - (float)cz;
+            wxs[u] = sx - (float)cx; wys[u] = sy - (float)cy; wzs[u] = sz - (float)cz;
             lx = (unsigned)(cx - lox); ly = (unsigned)(cy - loy); lz = (unsigned)(cz - loz);
           }
-          const float g0 = __uint_as_float(d << 16), g1 = __uint_as_float(d & 0xffff0000u);
-          if (boxed && lx < (unsigned)(nxb - 1) && ly < (unsigned)(nyb - 1) && lz < (unsigned)(nzb - 1)) {
-            const float ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
-            const float zy0 = az * ay, zy1 = az * wy, zy2 = wz * ay, zy3 = wz * wy;
-            const float gs0 = g0 * scale, gs1 = g1 * scale;
-            const uint32_t a0 = col_s + ((lz * (unsigned)nyb + ly) * (unsigned)nxb + lx) * kNodeBytes;
-            red_pair<C>(a0, zy0 * ax, zy0 * wx, gs0, gs1);
-            red_pair<C>(a0 + oy, zy1 * ax, zy1 * wx, gs0, gs1);
-            red_pair<C>(a0 + oz, zy2 * ax, zy2 * wx, gs0, gs1);
-            red_pair<C>(a0 + oy + oz, zy3 * ax, zy3 * wx, gs0, gs1);
-          } else {   // outside the tile's box (rounding at its faces, or an unsorted batch)
-            scatter_point(dFi, make_cell(ux, uy, uz, R), R, C, g0, C == 2 ? g1 : 0.f);
+          const bool inbox = boxed && lx < (unsigned)(nxb - 1) && ly < (unsigned)(nyb - 1) && lz < (unsigned)(nzb - 1);
+          ad[u] = in && inbox ? col_s + ((lz * (unsigned)nyb + ly) * (unsigned)nxb + lx) * kNodeBytes : ~0u;
+          live |= (uint32_t)in << u;
+        }
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+          if (ad[u] != ~0u) {
+            red_cell<C>(ad[u], oy, oz, wxs[u], wys[u], wzs[u], dc[u], scale);
+          } else if (live & (1u << u)) {   // outside the tile's box (rounding at its faces, or an unsorted batch)
+            const float4 x = h.xs[p + u * mp.npg];
+            float ux, uy, uz;
+            affine(gi, x.x, x.y, x.z, ux, uy, uz);
+            const uint32_t d = dc[u];
+            scatter_point(dFi, make_cell(ux, uy, uz, R), R, C, __uint_as_float(d << 16),
+                          C == 2 ? __uint_as_float(d & 0xffff0000u) : 0.f);
           }
         }
       }
