@@ -11,12 +11,14 @@
 //          K = 128 runs on tcgen05 instead (k_mlp_tc.cu).
 //  k_scat  adjoint of Eq. 2.  A tile is up to tile_points (<= 1024) points of one brick
 //          lying in one aligned Morton range of the sampler's bins (a small
-//          axis-aligned block of the brick), listed by k_unit_starts / k_tile_list.  Lane l of a warp takes
-//          grid l (of a group of 32): the block, mapped through the grid's Eq. 1,
+//          axis-aligned block of the brick), listed by k_unit_starts / k_tile_list.
+//          Two CTAs per SM take (tile, group of 32 grids) units.  Lane l of a warp
+//          takes grid l of the group: the block, mapped through the grid's Eq. 1,
 //          bounds a node box that the tile's level keeps within shared memory, and the
 //          warp adds one point's eight corners into 32 grids' boxes at once, as 32-bit
-//          fixed-point integers (a power-of-two scale per grid and tile from its
-//          largest |dL/dy|) with shared-memory integer reductions, one bank per lane.
+//          fixed-point integers (a power-of-two scale per grid and tile from a bound on
+//          its largest |dL/dy|: for K = 128 the decoder's maxima per 128 points) with
+//          shared-memory integer reductions, one bank per lane.
 //          Each box node then goes into the float32 gradient grid with one atomic.
 //          Points outside their tile's box (rounding at its faces; a batch that is not
 //          Morton-sorted) add their corners directly.
@@ -359,16 +361,19 @@ k_mlp(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ targ
 
 // =============================================================================== k_scat
 constexpr int ST = kMaxTilePoints;   // Morton-consecutive points per tile (at most)
-constexpr int SNT = 512;        // threads of k_scat (one CTA per SM)
+constexpr int SNT = 512;        // threads of k_enc (two CTAs per SM)
 constexpr int SNW = SNT / 32;
+constexpr int SCT = 256;        // threads of k_scat (two CTAs per SM)
+constexpr int SCW = SCT / 32;
 
-// Head of k_scat's dynamic shared memory; the tile's fixed-point node boxes follow it,
-// [group][node][channel][32 columns] int32 (see ScatMap).
+// Head of k_scat's dynamic shared memory; the unit's fixed-point node boxes follow it,
+// [node][channel][32 columns] int32 (see ScatMap).
 struct ScatHead {
   float4 xs[ST];               // the tile's points
-  uint2 box[kMaxGrids];        // node box of the tile's block per grid: lo | nodes per axis (bytes)
-  uint32_t gmax[kMaxGrids];    // largest |dL/dy| of the tile per grid (bf16 bits)
-  ScatTile tile, tnext;         // this tile, and the next one (taken one ahead)
+  uint2 box[32];               // node box of the tile's block per grid of the unit: lo | nodes per axis (bytes)
+  uint32_t gmax[32];           // largest |dL/dy| of the tile per grid of the unit (bf16 bits)
+  ScatTile tile, tnext;         // this unit's tile, and the next unit's (taken one ahead)
+  int grp, gnext;               // their column groups
 };
 
 // Thread -> grid, column group and point group of k_scat.  With M >= 32 the lanes of a
@@ -379,6 +384,25 @@ struct ScatHead {
 struct ScatMap {
   int g, grp, pg, npg;
 };
+// k_scat's units are (tile, column group): with M >= 32 a CTA takes the 32 grids of
+// group grp and its warps split the tile's points; with M < 32 (one group) lane l takes
+// grid l mod M and a warp 32/M points at a time.
+__device__ __forceinline__ ScatMap scat_unit_map(int M, int grp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ScatMap m;
+  if (M >= 32) {
+    m.grp = grp;
+    m.g = grp * 32 + lane;
+    m.pg = warp;
+    m.npg = SCW;
+  } else {
+    m.grp = 0;
+    m.g = lane % M;
+    m.pg = warp * (32 / M) + lane / M;
+    m.npg = SCW * (32 / M);
+  }
+  return m;
+}
 __device__ __forceinline__ ScatMap scat_map(int M) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   ScatMap m;
@@ -622,8 +646,9 @@ __device__ uint2 tile_box(uint32_t code, const float* __restrict__ g, int R) {
   return block_box(lo, hi, g, R);
 }
 
-// At most 96 registers: with them a CTA of the density pass (8 warps x 64) fits beside
-// the scatter's 16 warps in one SM's register file.
+// Two CTAs of 8 warps per SM, each on its own units, so that one CTA's barriers and
+// flushes overlap the other's reductions.  At most 96 registers: with them a CTA of the
+// density pass (8 warps x 64) fits beside the scatter's 16 warps in one SM's register file.
 template <int C, bool EVEN_R>
 __global__ void __maxnreg__(96)
 k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn) {
@@ -636,34 +661,38 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
   if (threadIdx.x == 0) build_tile_map(br, 128, dtm);
   const int tid = threadIdx.x, lane = tid & 31;
   const int M = md.M, R = md.R;
-  const ScatMap mp = scat_map(M);
   const int ngrp = M >= 32 ? M >> 5 : 1;
+  const int gper = M >= 32 ? 32 : M;             // grids of a unit
   constexpr int kNode = C * 32;                  // words of one node of a column group
   constexpr uint32_t kNodeBytes = kNode * 4;
   {  // the boxes start zeroed; every flush leaves them zeroed again
     uint4* a4 = reinterpret_cast<uint4*>(acc);
-    for (int q = tid; q < ngrp * capn * kNode / 4; q += SNT) a4[q] = make_uint4(0u, 0u, 0u, 0u);
+    for (int q = tid; q < capn * kNode / 4; q += SCT) a4[q] = make_uint4(0u, 0u, 0u, 0u);
   }
-  const int ntiles = ws.tile_ctr[0];
+  const int nunits = ws.tile_ctr[0] * ngrp;
   const int64_t gsz = (int64_t)R * R * R * C;
-  int32_t* col = acc + mp.grp * capn * kNode + lane;         // this thread's column
+  int32_t* col = acc + lane;                     // this thread's column
   const uint32_t col_s = su32(col);
   constexpr uint32_t kNz = C == 2 ? 0x7fff7fffu : 0x7fffu;    // nonzero dL/dy
   bool first = true;
   for (;;) {
-    // tiles are taken in list order (brick by brick, Morton order inside a brick), so
-    // the CTAs on the GPU at one time work on neighbouring blocks of one brick; each CTA
-    // takes its next tile one ahead and asks L2 for that tile's dL/dy rows (contiguous)
+    // units are taken in list order (brick by brick, Morton order inside a brick, the
+    // groups of a tile one after the other), so the CTAs on the GPU at one time work on
+    // neighbouring blocks of one brick; each CTA takes its next unit one ahead and asks
+    // L2 for that tile's dL/dy rows (contiguous)
     if (tid == 0) {
-      auto take = [&]() {
+      auto take = [&](int& grp) {
         const int t = atomicAdd(ws.tile_ctr + 1, 1);
         ScatTile T;
         T.start = 0; T.count = -1; T.code = 0;
-        if (t < ntiles) T = ws.tiles[t];
+        grp = 0;
+        if (t < nunits) { T = ws.tiles[t / ngrp]; grp = t % ngrp; }
         return T;
       };
-      h.tile = first ? take() : h.tnext;
-      h.tnext = h.tile.count < 0 ? h.tile : take();
+      if (first) h.tile = take(h.grp);
+      else { h.tile = h.tnext; h.grp = h.gnext; }
+      if (h.tile.count < 0) { h.tnext = h.tile; h.gnext = 0; }
+      else h.tnext = take(h.gnext);
       if (h.tnext.count > 0) {
         const char* rows = reinterpret_cast<const char*>(ws.dY + h.tnext.start * md.K);
         const uint32_t bytes = (uint32_t)h.tnext.count * (uint32_t)md.K * 2u;   // a multiple of 16
@@ -676,24 +705,27 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
     __syncthreads();   // also: the previous tile's flush has finished with h
     const ScatTile T = h.tile;
     if (T.count < 0) break;
+    const ScatMap mp = scat_unit_map(M, h.grp);
+    const int g0u = mp.grp * 32;                  // the unit's first grid (M >= 32)
     const int b = (int)(T.code >> 20);
     const int64_t p0 = T.start;
     const int np = T.count;
     const float* Gb = md.G + (int64_t)b * md.sG;
     const int lvl = (int)((T.code >> 16) & 15u);
     bool mine_in = true;   // every point of this thread lies in the tile's block
-    for (int p = tid; p < np; p += SNT) {
+    for (int p = tid; p < np; p += SCT) {
       const float x = xyz[3 * (p0 + p)], y = xyz[3 * (p0 + p) + 1], z = xyz[3 * (p0 + p) + 2];
       h.xs[p] = make_float4(x, y, z, 0.f);
       mine_in &= (((morton_bin(x, y, z) >> 3) ^ (T.code & 0xffffu)) >> lvl) == 0u;
     }
-    if (tid < M) {
-      h.box[tid] = tile_box(T.code, Gb + 12 * tid, R);
+    if (tid < gper) {
+      const int g = g0u + tid;
+      h.box[tid] = tile_box(T.code, Gb + 12 * g, R);
       uint32_t mb = 0u;
       if (ws.gmax_blk) {   // the decoder's maxima of the 128-point tiles overlapping this tile
         const int64_t lp = p0 - br.off[b];
         const int d0 = dtm.first[b] + (int)(lp / 128), d1 = dtm.first[b] + (int)((lp + np - 1) / 128);
-        for (int d = d0; d <= d1; ++d) mb = max(mb, (uint32_t)ws.gmax_blk[(int64_t)d * M + tid]);
+        for (int d = d0; d <= d1; ++d) mb = max(mb, (uint32_t)ws.gmax_blk[(int64_t)d * M + g]);
       }
       h.gmax[tid] = mb;
     }
@@ -714,15 +746,15 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
         for (int u = 0; u < 8; ++u) mx = C == 2 ? __vmaxu2(mx, d[u]) : max(mx, d[u]);
       }
       if (C == 2) mx = max(mx & 0xffffu, mx >> 16);
-      if (mx) atomicMax(h.gmax + mp.g, mx);
+      if (mx) atomicMax(h.gmax + (mp.g - g0u), mx);
     }
     __syncthreads();
-    const uint2 bx = h.box[mp.g];
+    const uint2 bx = h.box[mp.g - g0u];
     const int nxb = (int)(bx.y & 0xffu), nyb = (int)((bx.y >> 8) & 0xffu), nzb = (int)((bx.y >> 16) & 0xffu);
     const int lox = (int)(bx.x & 0xffu), loy = (int)((bx.x >> 8) & 0xffu), loz = (int)((bx.x >> 16) & 0xffu);
     const int nodes = nxb * nyb * nzb;
     const bool boxed = nodes > 0 && nodes <= capn;
-    const uint32_t mb = h.gmax[mp.g];
+    const uint32_t mb = h.gmax[mp.g - g0u];
     float inv;
     const float scale = fixed_scale(mb, np, inv);
     float* dFi = gr.dF + (int64_t)b * gr.sF + mp.g * gsz;
@@ -804,13 +836,13 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
     // flush: every nonzero node of the grid's box into the float32 gradient grid with one
     // atomic, summing the grid's columns (M < 32) and clearing them for the next tile
     if (boxed && mb != 0u && (M >= 32 || lane < M)) {
-      const int step = M >= 32 ? mp.npg : SNW;   // M < 32: lanes >= M idle, warps split the nodes
+      const int step = M >= 32 ? mp.npg : SCW;   // M < 32: lanes >= M idle, warps split the nodes
       const int n0 = M >= 32 ? mp.pg : (tid >> 5);
       int qz = n0 / (nxb * nyb), qr = n0 - qz * nxb * nyb;
       int qy = qr / nxb, qx = qr - qy * nxb;
       for (int n = n0; n < nodes; n += step) {
         int32_t s0 = 0, s1 = 0;
-        int32_t* q = acc + mp.grp * capn * kNode + n * kNode + lane;   // column lane = grid g's first
+        int32_t* q = acc + n * kNode + lane;   // column lane = grid g's first
         for (int sub = 0; sub < (M >= 32 ? 1 : 32 / M); ++sub) {
           int32_t* qs = q + sub * M;
           s0 += qs[0];
@@ -1015,11 +1047,11 @@ int occupancy(const void* kern, int threads, size_t smem) {
   return n;
 }
 
-// Dynamic shared memory of k_scat for boxes of capn nodes, and the largest capn that
-// the device's per-block limit allows beside the kernel's static shared memory.
+// Dynamic shared memory of k_scat for boxes of capn nodes (one column group), and the
+// largest capn with which two of its CTAs and one CTA of the density pass fit on an SM.
 size_t scat_smem(int M, int C, int capn) {
-  const int ngrp = M >= 32 ? M / 32 : 1;
-  return sizeof(ScatHead) + (size_t)ngrp * capn * C * 128;
+  (void)M;
+  return sizeof(ScatHead) + (size_t)capn * C * 128;
 }
 int scat_capn(int M, int C) {
   int dev = 0, optin = 0, per_sm = 0, stat = 0;
@@ -1028,11 +1060,12 @@ int scat_capn(int M, int C) {
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, (const void*)k_scat<2, true>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
-  const int ngrp = M >= 32 ? M / 32 : 1;
-  // leave room for one CTA of the density pass that may run beside the scatter
-  const long long block = std::min<long long>(optin, (long long)per_sm - 1024 - kDensityCtaSmem);
+  (void)M;
+  // two CTAs (1 KB reserved for each) and room for one CTA of the density pass that may
+  // run beside them (its reserve included)
+  const long long block = std::min<long long>(optin, ((long long)per_sm - 2 * 1024 - kDensityCtaSmem) / 2);
   const long long room = block - stat - (long long)sizeof(ScatHead);
-  return room > 0 ? (int)(room / ((long long)ngrp * C * 128)) : 0;
+  return room > 0 ? (int)(room / ((long long)C * 128)) : 0;
 }
 
 // The same for k_enc, at two CTAs per SM.
@@ -1137,10 +1170,10 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
                                  : (even ? (const void*)k_scat<1, true> : (const void*)k_scat<1, false>);
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    const int grid = L.num_sms * occupancy(kern, SNT, smem);
+    const int grid = L.num_sms * occupancy(kern, SCT, smem);
     mark_start(2);
     void* args[] = {(void*)&md, (void*)&gr, (void*)&br, (void*)&ws, (void*)&xyz, (void*)&capn};
-    if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(SNT), args, smem, L.stream)) != cudaSuccess) return e;
+    if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(SCT), args, smem, L.stream)) != cudaSuccess) return e;
     mark_stop(2);
   }
   if (ws.rec_dg) {
