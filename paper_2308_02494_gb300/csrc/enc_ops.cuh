@@ -1,8 +1,9 @@
 // The per-(point, grid) step of Eq. 1-2 of the BF16 training pass's encoder (k_enc): a
-// grid's node box over a tile of points is staged in shared memory as BF16 node values
-// (C per entry), node by node with one column per lane, so the eight corner reads of a
-// warp (32 lanes = 32 grids, one point) fall in 32 different banks.  A point whose cell
-// is not inside its grid's box takes the corners from global memory.
+// grid's node box over a tile of points is staged in shared memory as the float32
+// values of its BF16 nodes (C per entry: one 8-byte f32x2 pair for C = 2), node by node
+// with one column per lane, so the eight corner reads of a warp (32 lanes = 32 grids,
+// one point) fall in distinct banks, and each corner arrives as a ready f32x2 operand.
+// A point whose cell is not inside its grid's box takes the corners from global memory.
 #pragma once
 #include <type_traits>
 
@@ -27,7 +28,9 @@ __device__ __forceinline__ int32_t axis_cell(float u, float hs, float ct, float&
 }
 
 template <int C>
-using EncNode = std::conditional_t<C == 2, uint32_t, uint16_t>;   // one node: C bf16 values
+using EncNode = std::conditional_t<C == 2, uint32_t, uint16_t>;   // one node in global memory: C bf16 values
+template <int C>
+using EncSNode = std::conditional_t<C == 2, unsigned long long, float>;   // one staged node: C float32
 
 // Packed float pairs (two channels at once).
 __device__ __forceinline__ unsigned long long f2_bits(float lo, float hi) {
@@ -57,12 +60,12 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   return r;
 }
 
-// One staged node (C bf16 values) at shared address a + OFF.
+// One staged node (C float32 values) at shared address a + OFF.
 template <int C, int OFF>
-__device__ __forceinline__ uint32_t enc_node(uint32_t a) {
-  uint32_t v;
-  if constexpr (C == 2) asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
-  else asm volatile("ld.shared.u16 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+__device__ __forceinline__ EncSNode<C> enc_node(uint32_t a) {
+  EncSNode<C> v;
+  if constexpr (C == 2) asm volatile("ld.shared.b64 %0, [%1+%2];" : "=l"(v) : "r"(a), "n"(OFF));
+  else asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
   return v;
 }
 // Eq. 2 from the grid in global memory (a point outside its tile's box), packed as Y.
@@ -84,7 +87,7 @@ struct EncBox {
 };
 template <int C>
 __device__ __forceinline__ EncBox enc_box(uint2 bx, int capn, uint32_t col_s) {
-  constexpr uint32_t kRow = 32 * sizeof(EncNode<C>);   // bytes of one node row
+  constexpr uint32_t kRow = 32 * sizeof(EncSNode<C>);   // bytes of one node row
   EncBox e;
   e.nxb = (int)(bx.y & 0xffu); e.nyb = (int)((bx.y >> 8) & 0xffu); e.nzb = (int)((bx.y >> 16) & 0xffu);
   e.lox = (int)(bx.x & 0xffu); e.loy = (int)((bx.x >> 8) & 0xffu); e.loz = (int)((bx.x >> 16) & 0xffu);
@@ -98,11 +101,11 @@ __device__ __forceinline__ EncBox enc_box(uint2 bx, int capn, uint32_t col_s) {
 }
 
 // Stages one grid's node box (nodes of the box in x-fastest order) into this lane's
-// column: the threads of a grid group take nodes n0, n0 + nstep, ..., four loads in
-// flight.  Fg is the grid's BF16 nodes [R][R][R] (C per node).
+// column as float32: the threads of a grid group take nodes n0, n0 + nstep, ..., four
+// loads in flight.  Fg is the grid's BF16 nodes [R][R][R] (C per node).
 template <int C>
 __device__ __forceinline__ void enc_stage(const EncBox& e, const EncNode<C>* __restrict__ Fg, int R,
-                                          EncNode<C>* col, int n0, int nstep) {
+                                          EncSNode<C>* col, int n0, int nstep) {
   using E = EncNode<C>;
   const int nodes = e.nxb * e.nyb * e.nzb;
   int qz = n0 / (e.nxb * e.nyb), qr = n0 - qz * e.nxb * e.nyb;
@@ -120,8 +123,12 @@ __device__ __forceinline__ void enc_stage(const EncBox& e, const EncNode<C>* __r
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (n + u * nstep < nodes) col[(n + u * nstep) * 32] = v[u];
+    for (int u = 0; u < 4; ++u) {
+      if (n + u * nstep < nodes) {
+        if constexpr (C == 2) col[(n + u * nstep) * 32] = bf2_bits(v[u]);
+        else col[(n + u * nstep) * 32] = __uint_as_float((uint32_t)v[u] << 16);
+      }
+    }
   }
 }
 
@@ -132,7 +139,7 @@ __device__ __forceinline__ void enc_stage(const EncBox& e, const EncNode<C>* __r
 template <int C, bool EVEN_R>
 __device__ __forceinline__ uint32_t encode_point(const float (&gi)[12], float x, float y, float z, const EncBox& e,
                                                  float hs, float ct, int R, const __nv_bfloat16* Fi) {
-  constexpr uint32_t kRow = 32 * sizeof(EncNode<C>);
+  constexpr uint32_t kRow = 32 * sizeof(EncSNode<C>);
   float ux, uy, uz;
   affine(gi, x, y, z, ux, uy, uz);
   uint32_t yv = 0u;
@@ -158,18 +165,17 @@ __device__ __forceinline__ uint32_t encode_point(const float (&gi)[12], float x,
       const uint32_t a1 = a0 + e.oy, a2 = a0 + e.oz, a3 = a2 + e.oy;
       if constexpr (C == 2) {
         const unsigned long long px = f2_bits(wx, wx), py = f2_bits(wy, wy), pz = f2_bits(wz, wz);
-        const unsigned long long e0 = lerp2(bf2_bits(enc_node<C, 0>(a0)), bf2_bits(enc_node<C, kRow>(a0)), px);
-        const unsigned long long e1 = lerp2(bf2_bits(enc_node<C, 0>(a1)), bf2_bits(enc_node<C, kRow>(a1)), px);
-        const unsigned long long e2 = lerp2(bf2_bits(enc_node<C, 0>(a2)), bf2_bits(enc_node<C, kRow>(a2)), px);
-        const unsigned long long e3 = lerp2(bf2_bits(enc_node<C, 0>(a3)), bf2_bits(enc_node<C, kRow>(a3)), px);
+        const unsigned long long e0 = lerp2(enc_node<C, 0>(a0), enc_node<C, kRow>(a0), px);
+        const unsigned long long e1 = lerp2(enc_node<C, 0>(a1), enc_node<C, kRow>(a1), px);
+        const unsigned long long e2 = lerp2(enc_node<C, 0>(a2), enc_node<C, kRow>(a2), px);
+        const unsigned long long e3 = lerp2(enc_node<C, 0>(a3), enc_node<C, kRow>(a3), px);
         const unsigned long long f = lerp2(lerp2(e0, e1, py), lerp2(e2, e3, py), pz);
         yv = pack_bf16(__uint_as_float((uint32_t)f), __uint_as_float((uint32_t)(f >> 32)));
       } else {
-        auto v = [](uint32_t q) { return __uint_as_float(q << 16); };
-        const float v0 = v(enc_node<C, 0>(a0)), v1 = v(enc_node<C, kRow>(a0));
-        const float v2 = v(enc_node<C, 0>(a1)), v3 = v(enc_node<C, kRow>(a1));
-        const float v4 = v(enc_node<C, 0>(a2)), v5 = v(enc_node<C, kRow>(a2));
-        const float v6 = v(enc_node<C, 0>(a3)), v7 = v(enc_node<C, kRow>(a3));
+        const float v0 = enc_node<C, 0>(a0), v1 = enc_node<C, kRow>(a0);
+        const float v2 = enc_node<C, 0>(a1), v3 = enc_node<C, kRow>(a1);
+        const float v4 = enc_node<C, 0>(a2), v5 = enc_node<C, kRow>(a2);
+        const float v6 = enc_node<C, 0>(a3), v7 = enc_node<C, kRow>(a3);
         const float e0 = fmaf(wx, v1 - v0, v0), e1 = fmaf(wx, v3 - v2, v2);
         const float e2 = fmaf(wx, v5 - v4, v4), e3 = fmaf(wx, v7 - v6, v6);
         const float f01 = fmaf(wy, e1 - e0, e0), f23 = fmaf(wy, e3 - e2, e2);

@@ -376,47 +376,29 @@ struct ScatHead {
   int grp, gnext;               // their column groups
 };
 
-// Thread -> grid, column group and point group of k_scat.  With M >= 32 the lanes of a
-// warp take 32 consecutive grids (group w mod M/32) and the warps of a group split the
-// tile's points; with M < 32 lane l takes grid l mod M and a warp 32/M points at a time.
+// Thread -> grid, column group and point group of a unit of k_scat or k_enc (unit_map).
 // A grid group's boxes are stored node by node with one column per lane, so the 32
-// reductions of a warp instruction always fall in 32 different banks.
+// shared-memory accesses of a warp instruction fall in distinct banks.
 struct ScatMap {
   int g, grp, pg, npg;
 };
-// k_scat's units are (tile, column group): with M >= 32 a CTA takes the 32 grids of
-// group grp and its warps split the tile's points; with M < 32 (one group) lane l takes
-// grid l mod M and a warp 32/M points at a time.
-__device__ __forceinline__ ScatMap scat_unit_map(int M, int grp) {
+// The units of k_scat and k_enc are (tile, column group): with M >= 32 a CTA of NW
+// warps takes the 32 grids of group grp and its warps split the tile's points; with
+// M < 32 (one group) lane l takes grid l mod M and a warp 32/M points at a time.
+template <int NW>
+__device__ __forceinline__ ScatMap unit_map(int M, int grp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   ScatMap m;
   if (M >= 32) {
     m.grp = grp;
     m.g = grp * 32 + lane;
     m.pg = warp;
-    m.npg = SCW;
+    m.npg = NW;
   } else {
     m.grp = 0;
     m.g = lane % M;
     m.pg = warp * (32 / M) + lane / M;
-    m.npg = SCW * (32 / M);
-  }
-  return m;
-}
-__device__ __forceinline__ ScatMap scat_map(int M) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  ScatMap m;
-  if (M >= 32) {
-    const int ngrp = M >> 5;
-    m.grp = warp % ngrp;
-    m.g = m.grp * 32 + lane;
-    m.pg = warp / ngrp;
-    m.npg = SNW / ngrp;
-  } else {
-    m.grp = 0;
-    m.g = lane % M;
-    m.pg = warp * (32 / M) + lane / M;
-    m.npg = SNW * (32 / M);
+    m.npg = NW * (32 / M);
   }
   return m;
 }
@@ -705,7 +687,7 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
     __syncthreads();   // also: the previous tile's flush has finished with h
     const ScatTile T = h.tile;
     if (T.count < 0) break;
-    const ScatMap mp = scat_unit_map(M, h.grp);
+    const ScatMap mp = unit_map<SCW>(M, h.grp);
     const int g0u = mp.grp * 32;                  // the unit's first grid (M >= 32)
     const int b = (int)(T.code >> 20);
     const int64_t p0 = T.start;
@@ -865,50 +847,56 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
 }
 
 // =============================================================================== k_enc
-// Encoder (Eq. 1-3) on the scatter's tiles.  Lane l of a warp takes grid l of a group of
-// 32 (ScatMap).  Each grid's node box of the tile's block is staged in shared memory as
-// BF16 node values (C per entry), node by node with one column per lane, so the eight
-// corner reads of a warp fall in 32 different banks and the warp's features of one point
-// form one coalesced store of Y.  Points outside their box (rounding at its faces; an
-// unsorted batch) and grids whose box does not fit read the corners from global memory.
-// The feature density of Eq. 7 is a pass of its own (k_density_rho).
+// Encoder (Eq. 1-3) on the scatter's tiles, as (tile, group of 32 grids) units, two CTAs
+// of 16 warps per SM.  Lane l of a warp takes grid l of the unit's group (ScatMap).
+// Each grid's node box of the tile's block is staged in shared memory as the float32
+// values of its BF16 nodes (C per entry), node by node with one column per lane, so
+// the eight corner reads of a warp fall in distinct banks and the warp's features of
+// one point form one coalesced store of Y.  Points outside their box (rounding at its
+// faces; an unsorted batch) and grids whose box does not fit read the corners from
+// global memory.  The feature density of Eq. 7 is a pass of its own (k_density_rho).
 struct EncHead {
   float4 xs[ST];                // the tile's points
-  uint2 box[kMaxGrids];         // node box of the tile's block per grid (as in the scatter)
+  uint2 box[32];                // node box of the tile's block per grid of the unit (as in the scatter)
   float gs[kMaxGrids * 12];     // the brick's transforms
   ScatTile tile;
+  int grp;
 };
 template <int C, bool EVEN_R>
 __global__ void __launch_bounds__(SNT, 2)
 k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn) {
   using E = EncNode<C>;
+  using SE = EncSNode<C>;
   extern __shared__ __align__(16) unsigned char smraw[];
   EncHead& h = *reinterpret_cast<EncHead*>(smraw);
-  E* boxes = reinterpret_cast<E*>(smraw + sizeof(EncHead));   // [group][capn][32 columns]
+  SE* boxes = reinterpret_cast<SE*>(smraw + sizeof(EncHead));   // [capn][32 columns]
   __shared__ Bricks br;
   load_bricks(brp, br);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int M = md.M, R = md.R;
-  const ScatMap mp = scat_map(M);
-  const int ntiles = ws.tile_ctr[0];
+  const int ngrp = M >= 32 ? M >> 5 : 1;
+  const int gper = M >= 32 ? 32 : M;             // grids of a unit
+  const int nunits = ws.tile_ctr[0] * ngrp;
   const int64_t gsz = (int64_t)R * R * R * C;
-  E* col = boxes + mp.grp * capn * 32 + lane;             // this thread's column
+  SE* col = boxes + lane;                        // this thread's column
   const float hs = 0.5f * (float)(R - 1);
-  // staging: M >= 32, the warps of a group split the nodes of their grids; M < 32, every
-  // lane fills its own column and all warps split the nodes
-  const int n0 = M >= 32 ? mp.pg : warp, nstep = M >= 32 ? mp.npg : SNW;
+  // staging: every lane fills its own column, the warps split the nodes
+  const int n0 = warp, nstep = SNW;
   int cur = -1;
   for (;;) {
     if (tid == 0) {
       const int t = atomicAdd(ws.tile_ctr + 2, 1);
       ScatTile T;
       T.start = 0; T.count = -1; T.code = 0;
-      if (t < ntiles) T = ws.tiles[t];
+      h.grp = 0;
+      if (t < nunits) { T = ws.tiles[t / ngrp]; h.grp = t % ngrp; }
       h.tile = T;
     }
-    __syncthreads();   // also: the previous tile is done with h and the boxes
+    __syncthreads();   // also: the previous unit is done with h and the boxes
     const ScatTile T = h.tile;
     if (T.count < 0) break;
+    const ScatMap mp = unit_map<SNW>(M, h.grp);
+    const int g0u = mp.grp * 32;                  // the unit's first grid (M >= 32)
     const int b = (int)(T.code >> 20);
     const float* Gb = md.G + (int64_t)b * md.sG;
     if (b != cur) {
@@ -919,9 +907,9 @@ k_enc(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz, int capn)
     const int np = T.count;
     for (int p = tid; p < np; p += SNT)
       h.xs[p] = make_float4(xyz[3 * (p0 + p)], xyz[3 * (p0 + p) + 1], xyz[3 * (p0 + p) + 2], 0.f);
-    if (tid < M) h.box[tid] = tile_box(T.code, Gb + 12 * tid, R);
+    if (tid < gper) h.box[tid] = tile_box(T.code, Gb + 12 * (g0u + tid), R);
     __syncthreads();
-    const EncBox eb = enc_box<C>(h.box[mp.g], capn, su32(col));
+    const EncBox eb = enc_box<C>(h.box[mp.g - g0u], capn, su32(col));
     const E* Fg = reinterpret_cast<const E*>(md.F16 + (int64_t)b * md.sF + mp.g * gsz);
     if (eb.boxed) enc_stage<C>(eb, Fg, R, col, n0, nstep);
     float gi[12];
@@ -1070,8 +1058,8 @@ int scat_capn(int M, int C) {
 
 // The same for k_enc, at two CTAs per SM.
 size_t enc_smem(int M, int C, int capn) {
-  const int ngrp = M >= 32 ? M / 32 : 1;
-  return sizeof(EncHead) + (size_t)ngrp * capn * 32 * (C == 2 ? 4 : 2);
+  (void)M;
+  return sizeof(EncHead) + (size_t)capn * 32 * (C == 2 ? 8 : 4);
 }
 int enc_capn(int M, int C) {
   int dev = 0, per_sm = 0, stat = 0;
@@ -1079,9 +1067,9 @@ int enc_capn(int M, int C) {
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, (const void*)k_enc<2, true>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
-  const int ngrp = M >= 32 ? M / 32 : 1;
+  (void)M;
   const long long room = (long long)per_sm / 2 - 1024 - stat - (long long)sizeof(EncHead);
-  return room > 0 ? (int)(room / ((long long)ngrp * 32 * (C == 2 ? 4 : 2))) : 0;
+  return room > 0 ? (int)(room / ((long long)32 * (C == 2 ? 8 : 4))) : 0;
 }
 
 template <int K>
