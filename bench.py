@@ -51,8 +51,8 @@ KERNELS_PER_STEP = {"bf16": 15, "fp32": 10}
 # DRAM bytes (read + write) per launch of each training-pass kernel, from an ncu capture
 # of the 8-brick step (profiles/).  They hold only for the kernel sources they were
 # taken on: any change to those files makes bench report traffic as null.
-NCU_TRAFFIC = {"sources_sha1": "5dcaa2a6e3fd3ab7ff82f1e1cb33f27e36c9148d",
-               "k_scat": 1034.05e6, "k_enc": 715.97e6, "k_mlp": 1333.52e6}
+NCU_TRAFFIC = {"sources_sha1": "307d5b08c9f2d1611a21f2dda3268b62670b5464",
+               "k_scat": 1094.36e6, "k_enc": 715.91e6, "k_mlp": 1336.91e6}
 TRAFFIC_SOURCES = ("k_train_bf16.cu", "k_mlp_tc.cu", "common.cuh", "bf16_ops.cuh", "tc_ops.cuh", "enc_ops.cuh")
 
 
@@ -73,8 +73,8 @@ def measured_traffic(name):
 # lives in shared memory: the scatter adds 8 x C contributions with conflict-free
 # red.shared.add.u32 (measured on this GB300 with a probe of 16 warps per SM,
 # conflict-free addresses: 0.94 warp instructions per SM clock); the encoder reads 8
-# corners of C bf16 (one 4-byte word for C = 2) with conflict-free shared loads
-# (nominal: one warp instruction of 32 x 4 B per SM clock).
+# corners of C bf16 values (4 bytes per lane for C = 2; the kernel stages them as
+# float32, 8 bytes) at the nominal rate of one warp instruction of 32 x 4 B per SM clock.
 SMEM_RED_PER_CLK = 0.94
 SMEM_LDS_PER_CLK = 1.0
 FP32_LANES_PER_SM = 128
