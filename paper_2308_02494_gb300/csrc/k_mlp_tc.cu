@@ -17,6 +17,10 @@
 // atomic per entry when the CTA moves to another brick or finishes.  Every wait on
 // the tensor cores is bounded; on giving up the CTA sets bit 1 of the status word,
 // stops, and frees its tensor memory.
+#include <climits>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "bf16_ops.cuh"
 #include "kernels.h"
 #include "tc_ops.cuh"
@@ -41,11 +45,11 @@ struct TcLay {
   static constexpr uint32_t DW3 = W3 + 256;  // [64] f32 reduction scratch
   static constexpr uint32_t BYTES = DW3 + 256;
 };
-// Staging of dL/dy for its coalesced store: 16 chunk columns of 128 rows x 16 bytes,
-// padded by 16 bytes so both the row-wise writes and the chunk-wise reads are
-// conflict-free; it spans H1, DZ2 and part of DZ1, all free by then.
-constexpr uint32_t kDyStage = TcLay::H1, kDyChunkStride = 128 * 16 + 16;
-static_assert(kDyStage + 16 * kDyChunkStride <= TcLay::W3, "dL/dy staging overlaps w3");
+// Staging of dL/dy for the tensor store: the tile [128][128] bf16 in the operand layout
+// (two 1024-aligned blocks of 64 columns, the tensor map's 128-byte swizzle), over H1
+// and DZ2, both free by then.  Row-wise writes and chunk-wise reads are conflict-free.
+constexpr uint32_t kDyStage = TcLay::H1;
+static_assert(kDyStage % 1024 == 0 && TcLay::DZ2 == kDyStage + 16384, "dL/dy staging must be H1 then DZ2");
 // Tensor-memory columns.
 constexpr uint32_t kColZ1 = 0, kColZ2 = 64, kColDY = 0, kColDW1 = 128, kColDW2 = 192, kCols = 256;
 
@@ -73,14 +77,17 @@ __device__ __forceinline__ uint32_t nonzero_halves(uint32_t h) {
 
 // At most 200 registers: two CTAs (2 x 128 x 200) and one CTA of the density pass
 // beside them (256 x 56) fill the register file exactly.
+// tmY / tmDY: ws.Y and ws.dY as [points][128] bf16 tensors, boxes of 64 x 128 with the
+// 128-byte swizzle.
 __global__ void __maxnreg__(200)
-k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ target) {
+k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ target,
+         const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmDY) {
   extern __shared__ unsigned char raw[];
   __shared__ TileMap tm;
   __shared__ Bricks br;
   __shared__ uint32_t tslot;
   __shared__ uint32_t s_gmax[TK];   // largest |dL/dy| bits per grid of the tile being written
-  __shared__ __align__(8) unsigned long long mbar_s;
+  __shared__ __align__(8) unsigned long long mbar_s, mbar_y_s;
   load_bricks(brp, br);
   const uint32_t base0 = su32(raw), base = (base0 + 1023u) & ~1023u;
   unsigned char* sm = raw + (base - base0);
@@ -89,10 +96,11 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
   float* w3s = reinterpret_cast<float*>(sm + TcLay::W3);
   float* dw3s = reinterpret_cast<float*>(sm + TcLay::DW3);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t mbar = su32(&mbar_s);
+  const uint32_t mbar = su32(&mbar_s), mbar_y = su32(&mbar_y_s);
   if (tid == 0) {
     build_tile_map(br, TT, tm);
     tc::mbar_init(mbar, 1);
+    tc::mbar_init(mbar_y, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tc::tmem_alloc(su32(&tslot), kCols);
@@ -107,8 +115,8 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
   const int tb = blockIdx.x * per, te = min(total, tb + per);
   const int r = tid;   // the tile row this thread owns in the epilogues
 
-  uint32_t phase = 0;
-  bool gave_up = false;
+  uint32_t phase = 0, phase_y = 0;
+  bool gave_up = false, y_pending = false;
   auto wait_mma = [&]() {
     if (tc::mbar_wait(mbar, phase, kPolls)) phase ^= 1u;
     else gave_up = true;   // the phase stays: the final wait below retries it
@@ -169,8 +177,11 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     __syncthreads();
   };
 
-  // The features of tile t+1 are requested as soon as the last MMA of tile t has read
-  // Y, so the copy overlaps tile t's dL/dy epilogue; its targets likewise.
+  // The features of tile t+1 are requested (two tensor loads, 32 KB counted on mbar_y)
+  // as soon as the last MMA of tile t has read Y, so the copy overlaps tile t's dL/dy
+  // epilogue; its targets likewise.  Rows past the batch read as zero; rows past a
+  // brick's last point hold the next brick's features, which add nothing (their dL/dm
+  // is zero).
   int hint = -1;
   int64_t nxt_p0 = 0;
   int nxt_np = 0, nxt_b = 0;
@@ -180,12 +191,12 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     hint = nxt_b;
     nxt_p0 = br.off[nxt_b] + (int64_t)(tile - tm.first[nxt_b]) * TT;
     nxt_np = (int)min((int64_t)TT, br.off[nxt_b + 1] - nxt_p0);
-    for (int q = tid; q < TT * TK / 8; q += TNT) {
-      const int row = q >> 4, ch = q & 15;
-      const bool valid = row < nxt_np;
-      cp_async16(sY + tc::sw128_off(row, ch * 8, TT), ws.Y + (valid ? (nxt_p0 + row) * TK + ch * 8 : 0),
-                 valid ? 16 : 0);
+    if (tid == 0) {
+      tc::mbar_expect_tx(mbar_y, TT * TK * 2);
+      tc::tma_load_2d(sY, &tmY, mbar_y, 0, (int)nxt_p0);
+      tc::tma_load_2d(sY + TT * 128, &tmY, mbar_y, 64, (int)nxt_p0);
     }
+    y_pending = true;
     nxt_v = r < nxt_np ? target[nxt_p0 + r] : 0.f;
   };
   if (tb < te) prefetch(tb);
@@ -213,10 +224,17 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
       inv_n = 1.f / (float)(br.off[b + 1] - br.off[b]);
       fresh = true;
     }
-    // ---- the tile's features (requested one tile ahead; rows past np zero-filled)
+    // ---- the tile's features (requested one tile ahead); the previous tile's dL/dy
+    //      store has read its staging (H1 and DZ2, rewritten below)
     const bool rv = r < np;
-    cp_async_wait_all();
-    tc::fence_async_smem();
+    if (tc::mbar_wait(mbar_y, phase_y, kPolls)) {
+      phase_y ^= 1u;
+      y_pending = false;
+    } else {
+      gave_up = true;
+    }
+    if (tid == 0) tc::bulk_wait_read();
+    tc::fence_async_smem();   // a brick's weights, written above, are read by the MMAs
     tc::fence_before_sync();
     __syncthreads();
 
@@ -350,11 +368,9 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
     if (tile + 1 < te && !gave_up) prefetch(tile + 1);   // Y has been read by every MMA of this tile
     // ---- dL/dy to global memory, point-major bf16: row p0 + r holds the K features'
     //      gradients in feature order (grid-major, channel-minor, as Y).  Staged in the
-    //      (now free) H1 / dZ buffers as 16 column chunks of 16 bytes, chunk k of row r at
-    //      k * kDyChunkStride + 16 r (conflict-free both ways), then copied out with
-    //      coalesced stores: a warp writes two whole rows (512 contiguous bytes).  One
-    //      thread's row written with its own 16-byte stores would touch 32 scattered
-    //      sectors per warp instruction.
+    //      (now free) H1 / DZ2 buffers in the tensor map's swizzled layout, then written
+    //      by two tensor stores (thread 0) when the tile is full; a brick's last, partial
+    //      tile is copied out row by row, so that nothing lands on the next brick's rows.
 #pragma unroll 1
     for (int c0 = 0; c0 < TK; c0 += 32) {
       uint32_t za[16], zb[16], d[16];
@@ -368,23 +384,48 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4*>(sm + kDyStage + (c0 / 8 + q) * kDyChunkStride + 16 * r) =
+        *reinterpret_cast<uint4*>(sm + kDyStage + tc::sw128_off(r, c0 + 8 * q, TT)) =
             make_uint4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
     }
+    tc::fence_async_smem();
     __syncthreads();
-    {  // copy-out; thread t always handles chunk t mod 16, so it also takes the largest
-       // |dL/dy| of that chunk's features over the tile (for the scatter's fixed-point
-       // scales), reduced over the threads of the same chunk
+    const bool full = np == TT;
+    auto store_tile = [&]() {   // the full tile's two tensor stores, after the reads below
+      if (full && tid == 0) {
+        tc::tma_store_2d(&tmDY, base + kDyStage, 0, (int)p0);
+        tc::tma_store_2d(&tmDY, base + kDyStage + TT * 128, 64, (int)p0);
+        tc::bulk_commit();
+      }
+    };
+    if (!full || ws.gmax_blk) {
+      // thread t always reads chunk t mod 16, so it also takes the largest |dL/dy| of
+      // that chunk's features over the tile (for the scatter's fixed-point scales),
+      // reduced over the threads of the same chunk
       uint32_t mx[4] = {0u, 0u, 0u, 0u};
-      for (int q = tid; q < np * (TK / 8); q += TNT) {
-        const int row = q >> 4, k = q & 15;
-        const uint4 v = *reinterpret_cast<const uint4*>(sm + kDyStage + k * kDyChunkStride + 16 * row);
-        *reinterpret_cast<uint4*>(ws.dY + (p0 + row) * TK + 8 * k) = v;
+      auto take = [&](const uint4& v) {
         mx[0] = __vmaxu2(mx[0], v.x & 0x7fff7fffu);
         mx[1] = __vmaxu2(mx[1], v.y & 0x7fff7fffu);
         mx[2] = __vmaxu2(mx[2], v.z & 0x7fff7fffu);
         mx[3] = __vmaxu2(mx[3], v.w & 0x7fff7fffu);
+      };
+      if (full) {   // all 16 reads in flight at once (the tensor cores share these banks)
+        uint4 v[TT * TK / 8 / TNT];
+#pragma unroll
+        for (int i = 0; i < TT * TK / 8 / TNT; ++i) {
+          const int q = tid + i * TNT;
+          v[i] = *reinterpret_cast<const uint4*>(sm + kDyStage + tc::sw128_off(q >> 4, 8 * (q & 15), TT));
+        }
+#pragma unroll
+        for (int i = 0; i < TT * TK / 8 / TNT; ++i) take(v[i]);
+      } else {
+        for (int q = tid; q < np * (TK / 8); q += TNT) {
+          const int row = q >> 4, k = q & 15;
+          const uint4 v = *reinterpret_cast<const uint4*>(sm + kDyStage + tc::sw128_off(row, 8 * k, TT));
+          *reinterpret_cast<uint4*>(ws.dY + (p0 + row) * TK + 8 * k) = v;
+          take(v);
+        }
       }
+      store_tile();
       if (ws.gmax_blk) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) mx[j] = __vmaxu2(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], 16));
@@ -406,6 +447,8 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
           s_gmax[tid] = 0u;
         }
       }
+    } else {
+      store_tile();
     }
     fresh = false;
     tc::fence_before_sync();
@@ -420,12 +463,42 @@ k_mlp_tc(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ t
   } else if (cur >= 0) {
     flush(cur);
   }
-  cp_async_wait_all();   // a feature copy requested ahead may still be in flight
+  if (y_pending) tc::mbar_wait(mbar_y, phase_y, kPolls);   // a feature copy requested ahead (bounded)
+  if (tid == 0) tc::bulk_wait();                            // the last dL/dy stores are written
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, kCols);
 }
 
+}  // namespace
+
+namespace {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+// [rows][128] bf16 at base (rows 256 bytes apart) as a tensor of boxes 64 x 128 with the
+// 128-byte swizzle of the operand layout; reads outside the rows return zeros.
+cudaError_t feature_map(CUtensorMap* m, const void* base, int64_t rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)TK, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)TK * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)TT};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 }  // namespace
 
 // The decoder pass of the BF16 training step when K = 128 (2 CTAs per SM).
@@ -435,11 +508,16 @@ cudaError_t launch_mlp_tc(const Launch& L, const Model& md, const Grads& gr, con
   int tiles = 0;
   for (int b = 0; b < br.n; ++b) tiles += (int)((br.off[b + 1] - br.off[b] + TT - 1) / TT);
   if (tiles == 0) return cudaSuccess;
+  const int64_t rows = br.off[br.n];
+  if (rows > INT32_MAX) return cudaErrorInvalidValue;   // tensor coordinates are 32-bit
+  CUtensorMap tmY, tmDY;
+  cudaError_t e;
+  if ((e = feature_map(&tmY, ws.Y, rows)) != cudaSuccess) return e;
+  if ((e = feature_map(&tmDY, ws.dY, rows)) != cudaSuccess) return e;
   const int smem = (int)TcLay::BYTES + 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
   const int grid = std::min(tiles, 2 * L.num_sms);
-  k_mlp_tc<<<grid, TNT, smem, L.stream>>>(md, gr, br, ws, target);
+  k_mlp_tc<<<grid, TNT, smem, L.stream>>>(md, gr, br, ws, target, tmY, tmDY);
   return cudaGetLastError();
 }
 
