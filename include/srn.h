@@ -56,6 +56,8 @@ typedef enum { SRN_FP32 = 0, SRN_BF16 = 1 } srn_precision;
 #define SRN_SCHEDULE 4u  /* srn_train_step only: the training routine set by srn_set_schedule
                             decides, per brick on the device, whether G is trained and the
                             learning-rate scale; SRN_DENSITY is then ignored */
+#define SRN_VOLUME_TILED 16u /* srn_train_step only: volume_dev is the tiled copy written by
+                                srn_tile_volume (same dims), read by the ground-truth lookup */
 #define SRN_REC_DG 8u    /* srn_backward only: also the gradient of L_rec (or, with SRN_UPSTREAM,
                             of the upstream loss) with respect to G through Eq. 1-2, added into
                             G's gradient.  Sec. 4.3.2 trains G with L_den alone, so training
@@ -176,6 +178,24 @@ srn_status srn_sample_points_static(void* stream, uint64_t seed, uint64_t step, 
 srn_status srn_sample_target(srn_handle* h, void* stream, const float* volume_dev,
                              const int64_t dims[3], const int64_t* boxes,
                              const float* xyz_dev, const int64_t* offsets, float* target_dev);
+
+/* A tiled copy of a float32 volume for the ground-truth lookup v(x) of Sec. 4.3.1, which
+ * reads eight corners per point: the copy holds tiles of 4 x 4 x 4 voxels (tile
+ * (i, j, k) at tile index (k * ceil(dims[1]/4) + j) * ceil(dims[0]/4) + i, 64 floats per
+ * tile; inside a tile voxel (x, y, z) mod 4 at ((z * 4) + y) * 4 + x), each extent
+ * padded to whole tiles with zeros, so that a point's corners usually share one
+ * 256-byte tile instead of four rows far apart.  It is an input layout, not a cache:
+ * the copy reflects volume_dev when srn_tile_volume ran.
+ * srn_tiled_volume_bytes: the size of the copy for dims (each >= 2).
+ * srn_tile_volume: writes it (device memory, 16-byte aligned, of that size) on `stream`
+ * from the x-fastest volume_dev; does not need a handle.
+ * srn_sample_target_tiled: srn_sample_target reading such a copy (dims of the volume
+ * it came from); the results are identical. */
+srn_status srn_tiled_volume_bytes(const int64_t dims[3], size_t* bytes);
+srn_status srn_tile_volume(void* stream, const float* volume_dev, const int64_t dims[3], float* tiled_dev);
+srn_status srn_sample_target_tiled(srn_handle* h, void* stream, const float* tiled_dev,
+                                   const int64_t dims[3], const int64_t* boxes,
+                                   const float* xyz_dev, const int64_t* offsets, float* target_dev);
 
 /* Forward query f(x) = d(e(x)) (Eq. 1-3 and Sec. 4.1.2) of every brick's points:
  * out_dev[n] for xyz_dev[n].  offsets as in srn_sample_points. */

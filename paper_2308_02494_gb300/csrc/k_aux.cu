@@ -616,9 +616,21 @@ __global__ void k_sample_scatter(Bricks br, const float* __restrict__ tmp, const
 }
 
 // ------------------------------------------------------------ ground truth v(x)
+// Element offset of voxel (x, y, z) in the tiled layout of a volume whose x and y extents
+// span tx and ty tiles: tiles of kVolTile^3 voxels in x-fastest tile order, each tile's
+// voxels x-fastest.  The eight corners of a trilinear lookup then lie in one 256-byte
+// tile (and one DRAM page) unless the cell crosses a tile face.
+__device__ __forceinline__ int64_t tiled_offset(int64_t x, int64_t y, int64_t z, int64_t tx, int64_t ty) {
+  constexpr int S = kVolTile;
+  const int64_t t = ((z / S) * ty + (y / S)) * tx + (x / S);
+  return t * (S * S * S) + ((z % S) * S + (y % S)) * S + (x % S);
+}
+
+template <bool TILED>
 __global__ void k_target(Bricks br, const float* __restrict__ vol, int64_t dx, int64_t dy, int64_t dz,
                          VolumeBoxes vb, const float* __restrict__ xyz, float* __restrict__ out) {
   const int64_t total = br.off[br.n];
+  const int64_t tx = (dx + kVolTile - 1) / kVolTile, ty = (dy + kVolTile - 1) / kVolTile;
   for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x) {
     const int b = brick_of_point(br, gi);
     int c[3];
@@ -631,17 +643,35 @@ __global__ void k_target(Bricks br, const float* __restrict__ vol, int64_t dx, i
       c[d] = ci;
       w[d] = s - (float)ci;
     }
-    const int64_t base = ((int64_t)c[2] * dy + c[1]) * dx + c[0];
-    const int64_t sy = dx, sz = dx * dy;
-    const float v0 = __ldg(vol + base), v1 = __ldg(vol + base + 1);
-    const float v2 = __ldg(vol + base + sy), v3 = __ldg(vol + base + sy + 1);
-    const float v4 = __ldg(vol + base + sz), v5 = __ldg(vol + base + sz + 1);
-    const float v6 = __ldg(vol + base + sz + sy), v7 = __ldg(vol + base + sz + sy + 1);
+    float v[8];
+    if constexpr (TILED) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        v[k] = __ldg(vol + tiled_offset(c[0] + (k & 1), c[1] + ((k >> 1) & 1), c[2] + (k >> 2), tx, ty));
+    } else {
+      const int64_t base = ((int64_t)c[2] * dy + c[1]) * dx + c[0];
+      const int64_t sy = dx, sz = dx * dy;
+      v[0] = __ldg(vol + base); v[1] = __ldg(vol + base + 1);
+      v[2] = __ldg(vol + base + sy); v[3] = __ldg(vol + base + sy + 1);
+      v[4] = __ldg(vol + base + sz); v[5] = __ldg(vol + base + sz + 1);
+      v[6] = __ldg(vol + base + sz + sy); v[7] = __ldg(vol + base + sz + sy + 1);
+    }
     const float ax = 1.f - w[0], ay = 1.f - w[1], az = 1.f - w[2];
-    out[gi] = az * (ay * (ax * v0 + w[0] * v1) + w[1] * (ax * v2 + w[0] * v3)) +
-              w[2] * (ay * (ax * v4 + w[0] * v5) + w[1] * (ax * v6 + w[0] * v7));
+    out[gi] = az * (ay * (ax * v[0] + w[0] * v[1]) + w[1] * (ax * v[2] + w[0] * v[3])) +
+              w[2] * (ay * (ax * v[4] + w[0] * v[5]) + w[1] * (ax * v[6] + w[0] * v[7]));
   }
   (void)dz;
+}
+
+// The tiled copy of an x-fastest volume (its padding, zeroed beforehand, stays zero).
+__global__ void k_tile_volume(const float* __restrict__ vol, int64_t dx, int64_t dy, int64_t dz,
+                              float* __restrict__ out) {
+  const int64_t n = dx * dy * dz;
+  const int64_t tx = (dx + kVolTile - 1) / kVolTile, ty = (dy + kVolTile - 1) / kVolTile;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = i % dx, y = (i / dx) % dy, z = i / (dx * dy);
+    out[tiled_offset(x, y, z, tx, ty)] = vol[i];
+  }
 }
 
 int blocks_for(int64_t n, int threads, int num_sms, int per_sm) {
@@ -735,10 +765,24 @@ cudaError_t launch_sample(const Launch& L, const Bricks& br, unsigned long long 
 
 cudaError_t launch_target(const Launch& L, const Bricks& br, const float* vol, int64_t dx,
                           int64_t dy, int64_t dz, const VolumeBoxes& vb, const float* xyz,
-                          float* target) {
+                          float* target, bool tiled) {
   const int64_t total = br.off[br.n];
   if (total == 0) return cudaSuccess;
-  k_target<<<blocks_for(total, 256, L.num_sms, 8), 256, 0, L.stream>>>(br, vol, dx, dy, dz, vb, xyz, target);
+  const int blocks = blocks_for(total, 256, L.num_sms, 8);
+  if (tiled) k_target<true><<<blocks, 256, 0, L.stream>>>(br, vol, dx, dy, dz, vb, xyz, target);
+  else k_target<false><<<blocks, 256, 0, L.stream>>>(br, vol, dx, dy, dz, vb, xyz, target);
+  return cudaGetLastError();
+}
+
+int64_t tiled_volume_elems(int64_t dx, int64_t dy, int64_t dz) {
+  const int64_t S = kVolTile;
+  return ((dx + S - 1) / S) * ((dy + S - 1) / S) * ((dz + S - 1) / S) * S * S * S;
+}
+
+cudaError_t launch_tile_volume(const Launch& L, const float* vol, int64_t dx, int64_t dy, int64_t dz, float* out) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * tiled_volume_elems(dx, dy, dz), L.stream);
+  if (e != cudaSuccess) return e;
+  k_tile_volume<<<blocks_for(dx * dy * dz, 256, L.num_sms, 16), 256, 0, L.stream>>>(vol, dx, dy, dz, out);
   return cudaGetLastError();
 }
 

@@ -125,9 +125,15 @@ struct VolumeBoxes {
   int32_t lo[SRN_MAX_BRICKS][3];
   int32_t hi[SRN_MAX_BRICKS][3];
 };
+// v(x) by trilinear lookup; `tiled`: vol is in the layout launch_tile_volume writes.
 cudaError_t launch_target(const Launch& L, const Bricks& br, const float* vol, int64_t dx,
                           int64_t dy, int64_t dz, const VolumeBoxes& vb, const float* xyz,
-                          float* target);
+                          float* target, bool tiled);
+// The tiled layout of a dx x dy x dz volume: tiles of kVolTile^3 voxels (x-fastest tile
+// order, x-fastest inside a tile), each extent padded to whole tiles.
+constexpr int kVolTile = 4;
+int64_t tiled_volume_elems(int64_t dx, int64_t dy, int64_t dz);
+cudaError_t launch_tile_volume(const Launch& L, const float* vol, int64_t dx, int64_t dy, int64_t dz, float* out);
 
 // Sets the calling thread's srn_last_error() message and returns s.
 srn_status report(srn_status s, const char* message);

@@ -406,7 +406,7 @@ srn_status enqueue_train_step(srn_handle* h, void* stream, uint64_t seed, const 
                                      reinterpret_cast<uint32_t*>(ws + h->wl.sort_rank), hist);
   if (e != cudaSuccess) return cuda_fail(e, "sampler");
   // v(x) on the sorted batch (the volume reads of neighbouring points then share lines)
-  e = srn::launch_target(L, br, vol, dims[0], dims[1], dims[2], vb, xyz, target);
+  e = srn::launch_target(L, br, vol, dims[0], dims[1], dims[2], vb, xyz, target, (flags & SRN_VOLUME_TILED) != 0);
   if (e != cudaSuccess) return cuda_fail(e, "target lookup");
   // BF16 with the density loss: Adam of F and the decoder runs while the density
   // gradient (second stream) finishes; the transforms' Adam after the finalisation
@@ -598,8 +598,44 @@ srn_status srn_sample_target(srn_handle* h, void* stream, const float* vol, cons
   if ((s = make_boxes(h, dims, boxes, &vb)) != SRN_OK) return s;
   if (br.off[br.n] == 0) return SRN_OK;
   if (!vol || !xyz || !target) return fail(SRN_ERR_INVALID_ARG, "volume, xyz or target is NULL");
-  cudaError_t e = srn::launch_target(h->launch(stream), br, vol, dims[0], dims[1], dims[2], vb, xyz, target);
+  cudaError_t e = srn::launch_target(h->launch(stream), br, vol, dims[0], dims[1], dims[2], vb, xyz, target, false);
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "target lookup");
+}
+
+srn_status srn_sample_target_tiled(srn_handle* h, void* stream, const float* tiled, const int64_t dims[3],
+                                   const int64_t* boxes, const float* xyz, const int64_t* offsets, float* target) {
+  srn_status s = check_handle(h);
+  if (s != SRN_OK) return s;
+  srn::Bricks br;
+  srn::VolumeBoxes vb;
+  if ((s = make_bricks(h, offsets, &br)) != SRN_OK) return s;
+  if ((s = make_boxes(h, dims, boxes, &vb)) != SRN_OK) return s;
+  if (br.off[br.n] == 0) return SRN_OK;
+  if (!tiled || !xyz || !target) return fail(SRN_ERR_INVALID_ARG, "volume, xyz or target is NULL");
+  cudaError_t e = srn::launch_target(h->launch(stream), br, tiled, dims[0], dims[1], dims[2], vb, xyz, target, true);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "target lookup");
+}
+
+srn_status srn_tiled_volume_bytes(const int64_t dims[3], size_t* bytes) {
+  if (!dims || !bytes) return fail(SRN_ERR_INVALID_ARG, "dims or bytes is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (dims[d] < 2) return fail(SRN_ERR_INVALID_ARG, "volume dimension %d < 2", d);
+  *bytes = sizeof(float) * (size_t)srn::tiled_volume_elems(dims[0], dims[1], dims[2]);
+  return SRN_OK;
+}
+
+srn_status srn_tile_volume(void* stream, const float* vol, const int64_t dims[3], float* tiled) {
+  size_t bytes = 0;
+  srn_status s = srn_tiled_volume_bytes(dims, &bytes);
+  if (s != SRN_OK) return s;
+  if (!vol || !tiled) return fail(SRN_ERR_INVALID_ARG, "volume or tiled is NULL");
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = srn::launch_tile_volume(srn::Launch{static_cast<cudaStream_t>(stream), sms}, vol, dims[0], dims[1], dims[2],
+                                tiled);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "volume tiling");
 }
 
 srn_status srn_forward(srn_handle* h, void* stream, const float* xyz, const int64_t* offsets, float* out) {
@@ -644,7 +680,8 @@ srn_status srn_train_step(srn_handle* h, void* stream, uint64_t seed, const floa
   if ((s = check_training_counts(br)) != SRN_OK) return s;
   if ((s = make_boxes(h, dims, boxes, &vb)) != SRN_OK) return s;
   if (!vol || !xyz || !target) return fail(SRN_ERR_INVALID_ARG, "volume, xyz or target is NULL");
-  if (flags & ~(SRN_DENSITY | SRN_SCHEDULE)) return fail(SRN_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  if (flags & ~(SRN_DENSITY | SRN_SCHEDULE | SRN_VOLUME_TILED))
+    return fail(SRN_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
   if (flags & SRN_SCHEDULE) {
     if (!h->has_sched) return fail(SRN_ERR_STATE, "SRN_SCHEDULE before srn_set_schedule");
     if (!losses) return fail(SRN_ERR_INVALID_ARG, "SRN_SCHEDULE needs losses_dev");

@@ -21,6 +21,19 @@ def _stream_ptr(stream) -> int:
     return (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
 
 
+class TiledVolume:
+    """A volume in the tiled layout of srn_tile_volume (4^3-voxel tiles) for the ground-truth
+    lookup; `dims` are the (x, y, z) extents of the volume it was made from."""
+
+    def __init__(self, volume: torch.Tensor, stream=None):
+        if volume.dim() != 3 or volume.dtype != torch.float32 or not volume.is_contiguous():
+            raise ValueError("volume must be a contiguous float32 [z][y][x] tensor")
+        self.dims = [volume.shape[2], volume.shape[1], volume.shape[0]]
+        n = _s.srn_tiled_volume_bytes(self.dims) // 4
+        self.data = torch.empty(n, dtype=torch.float32, device=volume.device)
+        _s.srn_tile_volume(_stream_ptr(stream), volume.data_ptr(), self.dims, self.data.data_ptr())
+
+
 class SRN:
     def __init__(self, shape: ModelShape, n_bricks: int = 1, precision: str = "fp32",
                  max_points: int = 1 << 18, device="cuda", flat_top_p: int = 10,
@@ -156,9 +169,14 @@ class SRN:
         _s.srn_sample_points(self.handle, _stream_ptr(stream), seed, step, None, offsets, xyz.data_ptr())
         return xyz
 
-    def sample_target(self, volume: torch.Tensor, boxes, xyz, offsets, target=None, stream=None):
+    def sample_target(self, volume, boxes, xyz, offsets, target=None, stream=None):
+        """v(x) of every point; `volume` is a float32 [z][y][x] tensor or a TiledVolume."""
         if target is None:
             target = torch.empty(xyz.shape[0], dtype=torch.float32, device=self.device)
+        if isinstance(volume, TiledVolume):
+            _s.srn_sample_target_tiled(self.handle, _stream_ptr(stream), volume.data.data_ptr(), volume.dims,
+                                       np.asarray(boxes).ravel(), xyz.data_ptr(), offsets, target.data_ptr())
+            return target
         dims = [volume.shape[2], volume.shape[1], volume.shape[0]]
         _s.srn_sample_target(self.handle, _stream_ptr(stream), volume.data_ptr(), dims,
                              np.asarray(boxes).ravel(), xyz.data_ptr(), offsets, target.data_ptr())
@@ -182,9 +200,14 @@ class SRN:
         return _s.srn_rebalance(base_counts, self.read_schedule(stream), min_points)
 
     def train_step(self, seed, volume, boxes, offsets, density, xyz, target, stream=None, schedule=False):
-        dims = [volume.shape[2], volume.shape[1], volume.shape[0]]
+        """One srn_train_step; `volume` is a float32 [z][y][x] tensor or a TiledVolume."""
         flags = _s.SRN_SCHEDULE if schedule else (_s.SRN_DENSITY if density else 0)
-        _s.srn_train_step(self.handle, _stream_ptr(stream), seed, volume.data_ptr(), dims,
+        if isinstance(volume, TiledVolume):
+            dims, ptr = volume.dims, volume.data.data_ptr()
+            flags |= _s.SRN_VOLUME_TILED
+        else:
+            dims, ptr = [volume.shape[2], volume.shape[1], volume.shape[0]], volume.data_ptr()
+        _s.srn_train_step(self.handle, _stream_ptr(stream), seed, ptr, dims,
                           np.asarray(boxes).ravel(), offsets, flags,
                           xyz.data_ptr(), target.data_ptr(), self.losses.data_ptr())
         return self.losses

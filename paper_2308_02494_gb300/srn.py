@@ -27,6 +27,7 @@ SRN_DENSITY = 1
 SRN_UPSTREAM = 2
 SRN_SCHEDULE = 4
 SRN_REC_DG = 8
+SRN_VOLUME_TILED = 16
 SRN_MAX_BRICKS = 64
 
 # Every symbol include/srn.h declares (checked by the CPU tests).
@@ -36,7 +37,7 @@ EXPORTS = (
     "srn_step", "srn_train_step", "srn_render", "srn_set_timing", "srn_read_timing", "srn_get_status",
     "srn_sample_points_static", "srn_decode", "srn_state_bytes", "srn_save_state", "srn_load_state",
     "srn_set_schedule", "srn_read_schedule", "srn_render_progressive", "srn_get_tuning", "srn_set_tuning",
-    "srn_autotune", "srn_rebalance",
+    "srn_autotune", "srn_rebalance", "srn_tiled_volume_bytes", "srn_tile_volume", "srn_sample_target_tiled",
 )
 SRN_STATIC_SAMPLER_MAX_POINTS = 131072
 SRN_STATIC_SAMPLER_MAX_BRICKS = 8
@@ -109,6 +110,9 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
         "srn_sync_shadow": [P, P],
         "srn_sample_points": [P, P, U64, U64, P, I64P, P],
         "srn_sample_target": [P, P, P, I64P, I64P, P, I64P, P],
+        "srn_sample_target_tiled": [P, P, P, I64P, I64P, P, I64P, P],
+        "srn_tiled_volume_bytes": [I64P, ct.POINTER(ct.c_size_t)],
+        "srn_tile_volume": [P, P, I64P, P],
         "srn_forward": [P, P, P, I64P, P],
         "srn_backward": [P, P, P, P, I64P, U32, P],
         "srn_step": [P, P, U32],
@@ -188,6 +192,20 @@ def srn_sample_points(h, stream, seed, step, step_dev, offsets, xyz) -> None:
 
 def srn_sample_target(h, stream, volume, dims, boxes, xyz, offsets, target) -> None:
     _check(load().srn_sample_target(h, stream, volume, _i64(dims), _i64(boxes), xyz, _i64(offsets), target))
+
+
+def srn_sample_target_tiled(h, stream, tiled, dims, boxes, xyz, offsets, target) -> None:
+    _check(load().srn_sample_target_tiled(h, stream, tiled, _i64(dims), _i64(boxes), xyz, _i64(offsets), target))
+
+
+def srn_tiled_volume_bytes(dims) -> int:
+    n = ct.c_size_t()
+    _check(load().srn_tiled_volume_bytes(_i64(dims), ct.byref(n)))
+    return n.value
+
+
+def srn_tile_volume(stream, volume, dims, tiled) -> None:
+    _check(load().srn_tile_volume(stream, volume, _i64(dims), tiled))
 
 
 def srn_forward(h, stream, xyz, offsets, out) -> None:
