@@ -143,7 +143,11 @@ __device__ __forceinline__ uint32_t encode_point(const float (&gi)[12], float x,
   float ux, uy, uz;
   affine(gi, x, y, z, ux, uy, uz);
   uint32_t yv = 0u;
-  if ((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f)) {
+  // Eq. 2's mask.  With R even a cell in the box already means the point is inside the
+  // grid (the box's cells lie in [0, R-2], and beyond a face axis_cell gives -1 or R-1
+  // on that axis), so the mask is tested only for the points that miss the box.
+  const bool inside_now = EVEN_R || ((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f));
+  if (inside_now) {
     // Eq. 2's set-up: inside the grid s lies in [0, R-1] (the rounding of fmaf is
     // monotone).  R even: axis_cell.  R odd: the cell floor(s), which differs from
     // min(floor(s), R-2) only at s = R-1, whose cell R-1 is never in a box and takes
@@ -181,8 +185,8 @@ __device__ __forceinline__ uint32_t encode_point(const float (&gi)[12], float x,
         const float f01 = fmaf(wy, e1 - e0, e0), f23 = fmaf(wy, e3 - e2, e2);
         yv = __bfloat16_as_ushort(__float2bfloat16_rn(fmaf(wz, f23 - f01, f01)));
       }
-    } else {   // outside the box: the corners from global memory
-      yv = enc_global<C>(Fi, make_cell(ux, uy, uz, R), R);
+    } else if (!EVEN_R || ((fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f))) {
+      yv = enc_global<C>(Fi, make_cell(ux, uy, uz, R), R);   // outside the box: corners from global memory
     }
   }
   return yv;

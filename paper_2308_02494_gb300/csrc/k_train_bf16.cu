@@ -772,7 +772,7 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
         // dependency chains overlap; then the reductions point by point
         uint32_t ad[SU];            // box address of the cell's first corner; ~0u: not in the box
         float wxs[SU], wys[SU], wzs[SU];
-        uint32_t live = 0u;         // bit u: nonzero dL/dy and inside the grid
+        uint32_t live = 0u;         // bit u: nonzero dL/dy, cell not in the box (the direct path)
 #pragma unroll
         for (int u = 0; u < SU; ++u) {
           const int q = p + u * mp.npg;
@@ -783,7 +783,7 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
           // [0, R-1] already (the rounding of fmaf is monotone), so no clamp is needed
           // (with R odd the cell is floor(s): it differs from min(floor(s), R-2) only at
           // s = R-1, whose cell R-1 is never in a box and takes the exact path below)
-          const bool in = (dc[u] & kNz) && (fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f);
+          const bool nz = (dc[u] & kNz) != 0u;
           unsigned lx, ly, lz;   // cell relative to the box
           if constexpr (EVEN_R) {
             lx = (unsigned)(axis_cell(ux, hs, ct, wxs[u]) - mlox);
@@ -795,9 +795,13 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
             wxs[u] = sx - (float)cx; wys[u] = sy - (float)cy; wzs[u] = sz - (float)cz;
             lx = (unsigned)(cx - lox); ly = (unsigned)(cy - loy); lz = (unsigned)(cz - loz);
           }
-          const bool inbox = boxed && lx < (unsigned)(nxb - 1) && ly < (unsigned)(nyb - 1) && lz < (unsigned)(nzb - 1);
-          ad[u] = in && inbox ? col_s + ((lz * (unsigned)nyb + ly) * (unsigned)nxb + lx) * kNodeBytes : ~0u;
-          live |= (uint32_t)in << u;
+          bool inbox = boxed && lx < (unsigned)(nxb - 1) && ly < (unsigned)(nyb - 1) && lz < (unsigned)(nzb - 1);
+          // With R even a cell in the box means the point is inside the grid (Eq. 2's
+          // mask): the box's cells lie in [0, R-2], and beyond a face the cell on that
+          // axis is -1 or R-1.  With R odd the cell is a truncation: test the mask.
+          if constexpr (!EVEN_R) inbox = inbox && (fabsf(ux) <= 1.f) & (fabsf(uy) <= 1.f) & (fabsf(uz) <= 1.f);
+          ad[u] = nz && inbox ? col_s + ((lz * (unsigned)nyb + ly) * (unsigned)nxb + lx) * kNodeBytes : ~0u;
+          live |= (uint32_t)(nz && !inbox) << u;
         }
 #pragma unroll
         for (int u = 0; u < SU; ++u) {
@@ -807,9 +811,10 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
             const float4 x = h.xs[p + u * mp.npg];
             float ux, uy, uz;
             affine(gi, x.x, x.y, x.z, ux, uy, uz);
+            const Cell c = make_cell(ux, uy, uz, R);
             const uint32_t d = dc[u];
-            scatter_point(dFi, make_cell(ux, uy, uz, R), R, C, __uint_as_float(d << 16),
-                          C == 2 ? __uint_as_float(d & 0xffff0000u) : 0.f);
+            if (c.inside)
+              scatter_point(dFi, c, R, C, __uint_as_float(d << 16), C == 2 ? __uint_as_float(d & 0xffff0000u) : 0.f);
           }
         }
       }
