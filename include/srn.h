@@ -148,10 +148,10 @@ srn_status srn_sample_points(srn_handle* h, void* stream, uint64_t seed, uint64_
  * an interface convenience).  Some callers cannot allocate device memory at all -- a
  * plug-in running inside a host application that owns the GPU memory budget, or a
  * real-time loop whose allocator must not be entered -- so they cannot create a handle
- * with its workspace.  This entry point needs neither: its scratch (the unsorted draws,
- * each point's rank in its bin, and the bin histograms) is a file-scope __device__
- * array of 3 MiB that every GPU which loads the library holds until the process
- * exits.  It calls no allocation routine of any kind.
+ * with its workspace.  This entry point needs neither: its scratch (each point's rank
+ * in its bin and the bin histograms) is a file-scope __device__ array of 1.5 MiB that
+ * every GPU which loads the library holds until the process exits.  It calls no
+ * allocation routine of any kind.
  *   - At most SRN_STATIC_SAMPLER_MAX_POINTS points over at most
  *     SRN_STATIC_SAMPLER_MAX_BRICKS bricks; larger requests return SRN_ERR_INVALID_ARG.
  *   - Same draws and same per-brick Morton ordering as srn_sample_points with

@@ -38,24 +38,19 @@ __device__ __forceinline__ Tv warp_sum(Tv v) {
 constexpr int RHT = 256;   // threads; one CTA fits beside two decoder CTAs (at most 56 registers)
 constexpr int RHP = 2 * RHT;   // points per tile: two per thread, interleaved for latency
 
-// exp(-sum_d u_d^2p) of Eq. 7 for p = 10 (x and y axes as a packed pair) or any p
-template <bool P10>
-__device__ __forceinline__ float flat_top_value(float ux, float uy, float uz, int p) {
-  if constexpr (P10) {
-    const f2_t uxy = f2_pack(ux, uy), s2 = f2_mul(uxy, uxy);
-    f2_t q = f2_mul(s2, s2);
-    q = f2_mul(q, q);
-    q = f2_mul(q, q);
-    const f2_t p20 = f2_mul(f2_mul(q, s2), s2);
-    const float z2 = uz * uz;
-    float pz = z2 * z2;
-    pz = pz * pz;
-    pz = pz * pz;
-    const float ssum = fmaf(pz * z2, z2, f2_lo(p20) + f2_hi(p20));
-    return ssum <= 87.f ? __expf(-ssum) : 0.f;
-  } else {
-    return flat_top(ux, uy, uz, p);
-  }
+// exp(-sum_d u_d^2p) of Eq. 7 for p = 10, the x and y axes as a packed pair (ux, uy)
+__device__ __forceinline__ float flat_top_p10(f2_t uxy, float uz) {
+  const f2_t s2 = f2_mul(uxy, uxy);
+  f2_t q = f2_mul(s2, s2);
+  q = f2_mul(q, q);
+  q = f2_mul(q, q);
+  const f2_t p20 = f2_mul(f2_mul(q, s2), s2);
+  const float z2 = uz * uz;
+  float pz = z2 * z2;
+  pz = pz * pz;
+  pz = pz * pz;
+  const float ssum = fmaf(pz * z2, z2, f2_lo(p20) + f2_hi(p20));
+  return ssum <= 87.f ? __expf(-ssum) : 0.f;
 }
 
 template <bool P10>
@@ -94,8 +89,13 @@ k_density_rho(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
     if (b != cur) {
       if (cur >= 0) flush(cur);
       cur = b;
+      // each grid's map staged as the column pairs of its x and y rows, then its z row:
+      // [g0 g4 | g1 g5 | g2 g6 | g3 g7 | g8 g9 g10 g11] (g the row-major 3 x 4 map)
       const float* G = md.G + (int64_t)b * md.sG;
-      for (int k = tid; k < M * 12; k += RHT) sg[k] = G[k];
+      for (int k = tid; k < M * 12; k += RHT) {
+        const int i = k / 12, j = k - 12 * i;
+        sg[k] = G[12 * i + (j < 8 ? (j >> 1) + 4 * (j & 1) : j)];
+      }
       for (int i = tid; i < M; i += RHT) sdet[i] = det3(G + 12 * i);
       __syncthreads();
     }
@@ -104,17 +104,33 @@ k_density_rho(Model md, Bricks brp, TrainWs ws, const float* __restrict__ xyz) {
     const float xa = va ? xyz[3 * pa] : 0.f, ya = va ? xyz[3 * pa + 1] : 0.f, za = va ? xyz[3 * pa + 2] : 0.f;
     const float xb = vb ? xyz[3 * pb] : 0.f, yb = vb ? xyz[3 * pb + 1] : 0.f, zb = vb ? xyz[3 * pb + 2] : 0.f;
     float ra = 0.f, rb = 0.f;
+    if constexpr (P10) {   // Eq. 1's x and y rows as packed pairs: the point's coordinates doubled once
+      const f2_t xxa = f2_pack(xa, xa), yya = f2_pack(ya, ya), zza = f2_pack(za, za);
+      const f2_t xxb = f2_pack(xb, xb), yyb = f2_pack(yb, yb), zzb = f2_pack(zb, zb);
 #pragma unroll 2
-    for (int i = 0; i < M; ++i) {
-      const float4* g4 = reinterpret_cast<const float4*>(sg + 12 * i);
-      const float4 a = g4[0], c = g4[1], d = g4[2];
-      const float det = sdet[i];
-      ra = fmaf(det, flat_top_value<P10>(fmaf(a.x, xa, fmaf(a.y, ya, fmaf(a.z, za, a.w))),
-                                         fmaf(c.x, xa, fmaf(c.y, ya, fmaf(c.z, za, c.w))),
-                                         fmaf(d.x, xa, fmaf(d.y, ya, fmaf(d.z, za, d.w))), md.p), ra);
-      rb = fmaf(det, flat_top_value<P10>(fmaf(a.x, xb, fmaf(a.y, yb, fmaf(a.z, zb, a.w))),
-                                         fmaf(c.x, xb, fmaf(c.y, yb, fmaf(c.z, zb, c.w))),
-                                         fmaf(d.x, xb, fmaf(d.y, yb, fmaf(d.z, zb, d.w))), md.p), rb);
+      for (int i = 0; i < M; ++i) {
+        const ulonglong2 ab = *reinterpret_cast<const ulonglong2*>(sg + 12 * i);
+        const ulonglong2 cd = *reinterpret_cast<const ulonglong2*>(sg + 12 * i + 4);
+        const float4 z = *reinterpret_cast<const float4*>(sg + 12 * i + 8);
+        const float det = sdet[i];
+        ra = fmaf(det, flat_top_p10(f2_fma(ab.x, xxa, f2_fma(ab.y, yya, f2_fma(cd.x, zza, cd.y))),
+                                    fmaf(z.x, xa, fmaf(z.y, ya, fmaf(z.z, za, z.w)))), ra);
+        rb = fmaf(det, flat_top_p10(f2_fma(ab.x, xxb, f2_fma(ab.y, yyb, f2_fma(cd.x, zzb, cd.y))),
+                                    fmaf(z.x, xb, fmaf(z.y, yb, fmaf(z.z, zb, z.w)))), rb);
+      }
+    } else {
+#pragma unroll 2
+      for (int i = 0; i < M; ++i) {
+        const float4* g4 = reinterpret_cast<const float4*>(sg + 12 * i);
+        const float4 a = g4[0], c = g4[1], d = g4[2];   // (g0 g4 g1 g5), (g2 g6 g3 g7), (g8 .. g11)
+        const float det = sdet[i];
+        ra = fmaf(det, flat_top(fmaf(a.x, xa, fmaf(a.z, ya, fmaf(c.x, za, c.z))),
+                                           fmaf(a.y, xa, fmaf(a.w, ya, fmaf(c.y, za, c.w))),
+                                           fmaf(d.x, xa, fmaf(d.y, ya, fmaf(d.z, za, d.w))), md.p), ra);
+        rb = fmaf(det, flat_top(fmaf(a.x, xb, fmaf(a.z, yb, fmaf(c.x, zb, c.z))),
+                                           fmaf(a.y, xb, fmaf(a.w, yb, fmaf(c.y, zb, c.w))),
+                                           fmaf(d.x, xb, fmaf(d.y, yb, fmaf(d.z, zb, d.w))), md.p), rb);
+      }
     }
     if (va) { ws.rho[pa] = ra; sum += (double)ra; }
     if (vb) { ws.rho[pb] = rb; sum += (double)rb; }
@@ -544,21 +560,24 @@ __global__ void k_shadow(const float* __restrict__ p, uint16_t* __restrict__ sha
 }
 
 // ------------------------------------------------------------ sampler
+// Point n of brick b at sampler step s: one Philox4x32-10 block of counter (n, b, s, 0),
+// its first three words as 24-bit uniforms in [-1, 1).
+__device__ __forceinline__ float3 draw_point(uint32_t n, int b, unsigned long long s, uint2 key) {
+  const uint4 r = philox(make_uint4(n, (uint32_t)b, (uint32_t)s, 0u), key);
+  return make_float3(fmaf((float)(r.x >> 8), 0x1p-23f, -1.f), fmaf((float)(r.y >> 8), 0x1p-23f, -1.f),
+                     fmaf((float)(r.z >> 8), 0x1p-23f, -1.f));
+}
+
+// Counting sort, pass 1: each point's rank within its brick's Morton bin.
 __global__ void k_sample_gen(Bricks br, unsigned long long seed, unsigned long long step,
-                             const unsigned long long* step_dev, float* tmp, uint32_t* rank,
-                             uint32_t* hist) {
+                             const unsigned long long* step_dev, uint32_t* rank, uint32_t* hist) {
   const int64_t total = br.off[br.n];
   const unsigned long long s = step_dev ? *step_dev : step;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x) {
     const int b = brick_of_point(br, gi);
-    const uint32_t n = (uint32_t)(gi - br.off[b]);
-    const uint4 r = philox(make_uint4(n, (uint32_t)b, (uint32_t)s, 0u), key);
-    const float x = fmaf((float)(r.x >> 8), 0x1p-23f, -1.f);
-    const float y = fmaf((float)(r.y >> 8), 0x1p-23f, -1.f);
-    const float z = fmaf((float)(r.z >> 8), 0x1p-23f, -1.f);
-    tmp[3 * gi] = x; tmp[3 * gi + 1] = y; tmp[3 * gi + 2] = z;
-    rank[gi] = atomicAdd(hist + (int64_t)b * kSortBins + morton_bin(x, y, z), 1u);
+    const float3 p = draw_point((uint32_t)(gi - br.off[b]), b, s, key);
+    rank[gi] = atomicAdd(hist + (int64_t)b * kSortBins + morton_bin(p.x, p.y, p.z), 1u);
   }
 }
 
@@ -604,14 +623,19 @@ __global__ void __launch_bounds__(1024) k_sample_scan(uint32_t* hist) {
     h[k] = make_uint4(base + v[k].x, base + v[k].y, base + v[k].z, base + v[k].w);
 }
 
-__global__ void k_sample_scatter(Bricks br, const float* __restrict__ tmp, const uint32_t* __restrict__ rank,
+// Pass 2 (after the scan): the point drawn again (cheaper than storing and re-reading
+// it) and written at its bin's start plus its rank.
+__global__ void k_sample_scatter(Bricks br, unsigned long long seed, unsigned long long step,
+                                 const unsigned long long* step_dev, const uint32_t* __restrict__ rank,
                                  const uint32_t* __restrict__ hist, float* __restrict__ xyz) {
   const int64_t total = br.off[br.n];
+  const unsigned long long s = step_dev ? *step_dev : step;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x) {
     const int b = brick_of_point(br, gi);
-    const float x = tmp[3 * gi], y = tmp[3 * gi + 1], z = tmp[3 * gi + 2];
-    const int64_t dst = br.off[b] + hist[(int64_t)b * kSortBins + morton_bin(x, y, z)] + rank[gi];
-    xyz[3 * dst] = x; xyz[3 * dst + 1] = y; xyz[3 * dst + 2] = z;
+    const float3 p = draw_point((uint32_t)(gi - br.off[b]), b, s, key);
+    const int64_t dst = br.off[b] + hist[(int64_t)b * kSortBins + morton_bin(p.x, p.y, p.z)] + rank[gi];
+    xyz[3 * dst] = p.x; xyz[3 * dst + 1] = p.y; xyz[3 * dst + 2] = p.z;
   }
 }
 
@@ -749,17 +773,17 @@ cudaError_t launch_shadow(const Launch& L, const float* p, uint16_t* shadow, int
 
 cudaError_t launch_sample(const Launch& L, const Bricks& br, unsigned long long seed,
                           unsigned long long step, const unsigned long long* step_dev,
-                          float* xyz, float* tmp, uint32_t* rank, uint32_t* hist) {
+                          float* xyz, uint32_t* rank, uint32_t* hist) {
   const int64_t total = br.off[br.n];
   if (total == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kSortBins * br.n, L.stream);
   if (e != cudaSuccess) return e;
   const int blocks = blocks_for(total, 256, L.num_sms, 8);
-  k_sample_gen<<<blocks, 256, 0, L.stream>>>(br, seed, step, step_dev, tmp, rank, hist);
+  k_sample_gen<<<blocks, 256, 0, L.stream>>>(br, seed, step, step_dev, rank, hist);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_sample_scan<<<br.n, 1024, 0, L.stream>>>(hist);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_sample_scatter<<<blocks, 256, 0, L.stream>>>(br, tmp, rank, hist, xyz);
+  k_sample_scatter<<<blocks, 256, 0, L.stream>>>(br, seed, step, step_dev, rank, hist, xyz);
   return cudaGetLastError();
 }
 

@@ -120,7 +120,7 @@ cudaError_t launch_shadow(const Launch& L, const float* p, uint16_t* shadow, int
 // histogram the sampler leaves in `hist` holds each brick's bin starts.
 cudaError_t launch_sample(const Launch& L, const Bricks& br, unsigned long long seed,
                           unsigned long long step, const unsigned long long* step_dev,
-                          float* xyz, float* tmp, uint32_t* rank, uint32_t* hist);
+                          float* xyz, uint32_t* rank, uint32_t* hist);
 struct VolumeBoxes {
   int32_t lo[SRN_MAX_BRICKS][3];
   int32_t hi[SRN_MAX_BRICKS][3];

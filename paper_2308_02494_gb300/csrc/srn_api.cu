@@ -81,7 +81,7 @@ void make_layout(const srn_config* c, srn_layout* L) {
 
 // Workspace carving (every piece 256-byte aligned).
 struct WsLayout {
-  size_t state, acc, gsum, rsum, rho, herr, sort_tmp, sort_rank, sort_hist, feat, dfeat, gmax, ustart, tiles, tile_ctr;
+  size_t state, acc, gsum, rsum, rho, herr, sort_rank, sort_hist, feat, dfeat, gmax, ustart, tiles, tile_ctr;
   size_t sched, sring;
   size_t r_loc, r_rank, r_bid, r_pos, r_xyz, r_val, r_cnt, r_off, total;
 };
@@ -95,7 +95,6 @@ WsLayout ws_layout(const srn_config* c, int64_t maxp) {
   w.rsum = o; o += align256(sizeof(double) * 12 * c->n_grids * c->n_bricks);
   w.rho = o; o += align256(sizeof(float) * maxp);
   w.herr = o; o += align256(sizeof(float) * maxp);
-  w.sort_tmp = o; o += align256(sizeof(float) * 3 * maxp);
   w.sort_rank = o; o += align256(sizeof(uint32_t) * maxp);
   w.sort_hist = o; o += align256(sizeof(uint32_t) * srn::kSortBins * c->n_bricks);
   // BF16 training pass: features Y [N][K] and dL/dy [M][N][C], both bfloat16
@@ -402,7 +401,6 @@ srn_status enqueue_train_step(srn_handle* h, void* stream, uint64_t seed, const 
   unsigned char* ws = h->ws;
   uint32_t* hist = reinterpret_cast<uint32_t*>(ws + h->wl.sort_hist);
   cudaError_t e = srn::launch_sample(L, br, seed, 0, &h->state()->step, xyz,
-                                     reinterpret_cast<float*>(ws + h->wl.sort_tmp),
                                      reinterpret_cast<uint32_t*>(ws + h->wl.sort_rank), hist);
   if (e != cudaSuccess) return cuda_fail(e, "sampler");
   // v(x) on the sorted batch (the volume reads of neighbouring points then share lines)
@@ -581,7 +579,6 @@ srn_status srn_sample_points(srn_handle* h, void* stream, uint64_t seed, uint64_
   if (!xyz) return fail(SRN_ERR_INVALID_ARG, "xyz is NULL");
   cudaError_t e = srn::launch_sample(h->launch(stream), br, seed, step,
                                      reinterpret_cast<const unsigned long long*>(step_dev), xyz,
-                                     reinterpret_cast<float*>(h->ws + h->wl.sort_tmp),
                                      reinterpret_cast<uint32_t*>(h->ws + h->wl.sort_rank),
                                      reinterpret_cast<uint32_t*>(h->ws + h->wl.sort_hist));
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "sampler");

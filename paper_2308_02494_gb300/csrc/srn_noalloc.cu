@@ -1,8 +1,8 @@
 // srn_sample_points_static: the batch sampler for callers that cannot allocate device
 // memory.  It runs the same kernels as srn_sample_points (Philox4x32-10 draws, then a
-// counting sort of each brick's points by 32^3 Morton bin), but its scratch -- the
-// unsorted draws, each point's rank in its bin, and the bin histograms -- lives in one
-// file-scope __device__ array instead of a caller-allocated workspace.
+// counting sort of each brick's points by 32^3 Morton bin), but its scratch -- each
+// point's rank in its bin and the bin histograms -- lives in one file-scope __device__
+// array instead of a caller-allocated workspace.
 #include <mutex>
 
 #include "common.cuh"
@@ -12,12 +12,11 @@ namespace {
 
 constexpr int64_t kMaxPoints = SRN_STATIC_SAMPLER_MAX_POINTS;
 constexpr int kMaxBricks = SRN_STATIC_SAMPLER_MAX_BRICKS;
-constexpr size_t kTmpBytes = sizeof(float) * 3 * kMaxPoints;
 constexpr size_t kRankBytes = sizeof(uint32_t) * kMaxPoints;
 constexpr size_t kHistBytes = sizeof(uint32_t) * srn::kSortBins * kMaxBricks;
 
 // One copy per device that loads the library, held until the process exits.
-static __device__ __align__(256) unsigned char g_sampler_scratch[kTmpBytes + kRankBytes + kHistBytes];
+static __device__ __align__(256) unsigned char g_sampler_scratch[kRankBytes + kHistBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
@@ -73,10 +72,9 @@ extern "C" srn_status srn_sample_points_static(void* stream, uint64_t seed, uint
   if (e != cudaSuccess) return srn::report(SRN_ERR_CUDA, cudaGetErrorString(e));
   const srn::Launch L{static_cast<cudaStream_t>(stream), sms};
   // launch_sample clears the histograms (the only scratch that must start at zero)
-  // with cudaMemsetAsync before drawing; the draws and ranks are fully overwritten.
-  e = srn::launch_sample(L, br, seed, step, nullptr, xyz_dev, reinterpret_cast<float*>(scratch),
-                         reinterpret_cast<uint32_t*>(scratch + kTmpBytes),
-                         reinterpret_cast<uint32_t*>(scratch + kTmpBytes + kRankBytes));
+  // with cudaMemsetAsync before drawing; the ranks are fully overwritten.
+  e = srn::launch_sample(L, br, seed, step, nullptr, xyz_dev, reinterpret_cast<uint32_t*>(scratch),
+                         reinterpret_cast<uint32_t*>(scratch + kRankBytes));
   if (e != cudaSuccess) return srn::report(SRN_ERR_CUDA, cudaGetErrorString(e));
   return SRN_OK;
 }
