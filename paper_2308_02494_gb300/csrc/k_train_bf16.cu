@@ -755,11 +755,15 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
       // dL/dy of the next SU points is requested while the current SU are processed
       constexpr int SU = 4;
       uint32_t dn[SU];
+      // this lane's dL/dy of the tile's first point; point q's is q * M entries on
+      // (C bf16 per entry)
+      using DyT = std::conditional_t<C == 2, unsigned int, unsigned short>;
+      const DyT* dyl = reinterpret_cast<const DyT*>(ws.dY) + p0 * M + mp.g;
       auto load_next = [&](int p) {
 #pragma unroll
         for (int u = 0; u < SU; ++u) {
           const int q = p + u * mp.npg;
-          dn[u] = q < np ? dy_bits<C>(ws.dY, p0 + q, M, mp.g) : 0u;
+          dn[u] = q < np ? (uint32_t)__ldg(dyl + q * M) : 0u;
         }
       };
       load_next(mp.pg);
