@@ -115,7 +115,7 @@ __device__ __forceinline__ void enc_stage(const EncBox& e, const EncNode<C>* __r
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       v[u] = 0;
-      if (n + u * nstep < nodes) v[u] = __ldg(Fg + ((int64_t)(e.loz + qz) * R + (e.loy + qy)) * R + e.lox + qx);
+      if (n + u * nstep < nodes) v[u] = __ldg(Fg + ((e.loz + qz) * R + (e.loy + qy)) * R + e.lox + qx);   // < R^3
       qx += nstep;
       while (qx >= e.nxb) {
         qx -= e.nxb;

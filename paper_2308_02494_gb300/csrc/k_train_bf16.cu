@@ -841,7 +841,7 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
           if (C == 2) { s1 += qs[32]; qs[32] = 0; }
         }
         if (s0 | s1) {
-          const int64_t node = ((int64_t)(loz + qz) * R + (loy + qy)) * R + lox + qx;
+          const int node = ((loz + qz) * R + (loy + qy)) * R + lox + qx;   // < R^3 <= 2^18
           if (C == 2) atomicAdd(reinterpret_cast<float2*>(dFi) + node, make_float2((float)s0 * inv, (float)s1 * inv));
           else atomicAdd(dFi + node, (float)s0 * inv);
         }
