@@ -86,3 +86,16 @@ def test_create_rejects_null_tensors_without_touching_the_gpu(lib):
     st = lib.srn_create(ct.byref(_cfg()), ct.byref(t), None, 0, 16, ct.byref(h))
     assert st == srn.SRN_ERR_INVALID_ARG
     assert lib.srn_destroy(None) == srn.SRN_ERR_INVALID_ARG
+
+
+def test_tiled_volume_size_pads_each_extent_to_whole_tiles(lib):
+    # 4 x 4 x 4-voxel tiles of float32: ceil(d / 4) tiles per axis, 256 bytes per tile
+    for dims, tiles in [((4, 4, 4), 1), ((5, 4, 4), 2), ((5, 6, 7), 8), ((1024, 1024, 1024), 256 ** 3),
+                        ((2, 3, 9), 3), ((513, 2, 2), 129)]:
+        assert srn.srn_tiled_volume_bytes(list(dims)) == 256 * tiles, dims
+
+
+def test_tiled_volume_size_rejects_an_extent_below_two(lib):
+    with pytest.raises(srn.SrnError) as e:
+        srn.srn_tiled_volume_bytes([8, 1, 8])
+    assert "dimension 1" in str(e.value)
