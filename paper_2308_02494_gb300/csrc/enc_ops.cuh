@@ -60,6 +60,20 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   return r;
 }
 
+// axis_cell for two axes at once, u = (ua, ub) as a packed pair, hs2 = (hs, hs),
+// ct2 = (ct, ct), m2 = (kMagic, kMagic): the same roundings as two axis_cell calls.
+__device__ __forceinline__ void axis_cell2(unsigned long long u, unsigned long long hs2, unsigned long long ct2,
+                                           unsigned long long m2, int32_t& ta, int32_t& tb, float& wa, float& wb) {
+  const unsigned long long t = fma2(u, hs2, ct2), s = fma2(u, hs2, hs2);
+  unsigned long long tm, w;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(tm) : "l"(t), "l"(m2));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(w) : "l"(s), "l"(tm));
+  ta = (int32_t)(uint32_t)t;
+  tb = (int32_t)(uint32_t)(t >> 32);
+  wa = __uint_as_float((uint32_t)w);
+  wb = __uint_as_float((uint32_t)(w >> 32));
+}
+
 // One staged node (C float32 values) at shared address a + OFF.
 template <int C, int OFF>
 __device__ __forceinline__ EncSNode<C> enc_node(uint32_t a) {
@@ -155,8 +169,10 @@ __device__ __forceinline__ uint32_t encode_point(const float (&gi)[12], float x,
     float wx, wy, wz;
     unsigned lx, ly, lz;   // cell relative to the box
     if constexpr (EVEN_R) {
-      lx = (unsigned)(axis_cell(ux, hs, ct, wx) - e.mlox);
-      ly = (unsigned)(axis_cell(uy, hs, ct, wy) - e.mloy);
+      int32_t tx, ty;   // x and y as one packed pair
+      axis_cell2(f2_bits(ux, uy), f2_bits(hs, hs), f2_bits(ct, ct), f2_bits(kMagic, kMagic), tx, ty, wx, wy);
+      lx = (unsigned)(tx - e.mlox);
+      ly = (unsigned)(ty - e.mloy);
       lz = (unsigned)(axis_cell(uz, hs, ct, wz) - e.mloz);
     } else {
       const float sx = fmaf(ux, hs, hs), sy = fmaf(uy, hs, hs), sz = fmaf(uz, hs, hs);

@@ -751,6 +751,7 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
       const uint32_t oy = (uint32_t)nxb * kNodeBytes, oz = (uint32_t)(nxb * nyb) * kNodeBytes;
       const float hs = 0.5f * (float)(R - 1);
       const float ct = hs - 0.5f + kMagic;   // an integer when R is even (axis_cell)
+      const unsigned long long hs2 = f2_bits(hs, hs), ct2 = f2_bits(ct, ct), mm2 = f2_bits(kMagic, kMagic);
       const int32_t mlox = kMagicBits + lox, mloy = kMagicBits + loy, mloz = kMagicBits + loz;
       // dL/dy of the next SU points is requested while the current SU are processed
       constexpr int SU = 4;
@@ -790,8 +791,10 @@ k_scat(Model md, Grads gr, Bricks brp, TrainWs ws, const float* __restrict__ xyz
           const bool nz = (dc[u] & kNz) != 0u;
           unsigned lx, ly, lz;   // cell relative to the box
           if constexpr (EVEN_R) {
-            lx = (unsigned)(axis_cell(ux, hs, ct, wxs[u]) - mlox);
-            ly = (unsigned)(axis_cell(uy, hs, ct, wys[u]) - mloy);
+            int32_t tx, ty;   // x and y as one packed pair
+            axis_cell2(f2_bits(ux, uy), hs2, ct2, mm2, tx, ty, wxs[u], wys[u]);
+            lx = (unsigned)(tx - mlox);
+            ly = (unsigned)(ty - mloy);
             lz = (unsigned)(axis_cell(uz, hs, ct, wzs[u]) - mloz);
           } else {
             const float sx = fmaf(ux, hs, hs), sy = fmaf(uy, hs, hs), sz = fmaf(uz, hs, hs);
