@@ -51,8 +51,8 @@ KERNELS_PER_STEP = {"bf16": 15, "fp32": 10}
 # DRAM bytes (read + write) per launch of each training-pass kernel, from an ncu capture
 # of the 8-brick step (profiles/).  They hold only for the kernel sources they were
 # taken on: any change to those files makes bench report traffic as null.
-NCU_TRAFFIC = {"sources_sha1": "1cfb11e814ba63b75b062c73b27e86b8ea31bac5",
-               "k_scat": 1102.15e6, "k_enc": 715.13e6, "k_mlp": 1336.33e6}
+NCU_TRAFFIC = {"sources_sha1": "7fb69f7e343ca9564d9370a2b193190b7153834c",
+               "k_scat": 1082.62e6, "k_enc": 715.19e6, "k_mlp": 1336.33e6}
 TRAFFIC_SOURCES = ("k_train_bf16.cu", "k_mlp_tc.cu", "common.cuh", "bf16_ops.cuh", "tc_ops.cuh", "enc_ops.cuh")
 
 
