@@ -13,10 +13,14 @@
 // the brick's dW1^T and dW2^T accumulated across tiles in 128..255); thread r of the
 // CTA owns tile row r in every epilogue (tcgen05.ld of its tensor-memory lane),
 // applies ReLU / the loss / the masks and writes the next operand back to shared
-// memory as BF16.  The accumulated weight gradients go to global memory with one
-// atomic per entry when the CTA moves to another brick or finishes.  Every wait on
-// the tensor cores is bounded; on giving up the CTA sets bit 1 of the status word,
-// stops, and frees its tensor memory.
+// memory as BF16.  Y tiles arrive by TMA tensor loads counted on an mbarrier (the
+// tensor map's 128-byte swizzle is the operand layout), and dL/dy leaves by TMA tensor
+// stores from a swizzled stage, which is also read for the largest |dL/dy| of every
+// grid over the tile (the scatter's fixed-point scales).  The accumulated weight
+// gradients go to global memory with one atomic per entry when the CTA moves to
+// another brick or finishes.  Every wait on the tensor cores and on the tensor loads is
+// bounded; on giving up the CTA sets bit 1 of the status word, stops, and frees its
+// tensor memory.
 #include <climits>
 #include <cuda.h>
 #include <cudaTypedefs.h>
