@@ -1,9 +1,10 @@
 // BF16 training pass over all bricks: three kernels, each shaped for its own bound.
 //
-//  k_enc   encoder (Eq. 1-3) over the same tiles as k_scat, two CTAs per SM: each
-//          tile's node boxes of the BF16 grids are staged in shared memory (one column
-//          per lane), the corners blended as packed f32x2.  Writes the features
-//          Y [N][K] (bf16).  rho of Eq. 7 is a pass of its own (k_density_rho).
+//  k_enc   encoder (Eq. 1-3) over the same tiles as k_scat, as (tile, group of 32
+//          grids) units, two CTAs per SM: each unit's node boxes of the BF16 grids
+//          are staged in shared memory as float32 (one column per lane), the corners
+//          read and blended as packed f32x2.  Writes the features Y [N][K] (bf16).
+//          rho of Eq. 7 is a pass of its own (k_density_rho).
 //  k_mlp   decoder forward and backward for K < 128 on the tensor cores (mma.sync
 //          m16n8k16, BF16 operands, FP32 accumulation): L_rec partial sums,
 //          h(x) = (f - v)^2, dW1/dW2/dw3 accumulated in registers per CTA and flushed
@@ -1151,8 +1152,8 @@ cudaError_t launch_train_k(const Launch& L, bool dens, const Model& md, const Gr
   }
   if (dens && side) {   // the other two density passes beside the scatter, after the decoder
     // CTAs taking tiles from a counter, tn.density_ctas per SM (default two): one fits
-    // beside the scatter's CTA (registers and the shared memory scat_capn leaves), the
-    // other starts as the scatter's CTA finishes and leaves room for the Adam of F and
+    // beside the scatter's two CTAs (registers and the shared memory scat_capn leaves),
+    // the other starts as the scatter's CTAs finish and leaves room for the Adam of F and
     // the decoder, which the training step runs beside this pass's tail (measured: 3.43 ms
     // per step against 3.48 with four CTAs per SM, whose registers fill the SM)
     const int ctas = std::min(std::max(tn.density_ctas, 1), kMaxDensityCtas);
